@@ -1,0 +1,254 @@
+"""Pins for the CPU oracle, independent of the oracle itself.
+
+Each test checks the oracle against something the paper or plain mathematics
+fixes: the paper's running example (Sec. II Example 1, Sec. IV Example 2 and
+Table 1), SciPy's all-pairs shortest paths (a library routine, for d_v^h),
+closed forms on structured graphs, Definition 2 by exhaustion, the classic
+k-core at h = 1 (Sec. II: the (k,1)-core is the k-core) via networkx and the
+Batagelj-Zaversnik bin sort, and invariants of the model.
+"""
+import itertools
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+from scipy.sparse.csgraph import shortest_path
+
+import graphgen as gg
+import oracle
+from conftest import small_graphs
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+def scipy_hdeg(g, h, alive=None):
+    """d_v^h by SciPy's unweighted all-pairs shortest paths on G[alive]."""
+    n = g.n
+    alive = np.ones(n, bool) if alive is None else np.asarray(alive, bool)
+    src = np.repeat(np.arange(n), g.degrees())
+    A = sp.csr_matrix((np.ones(len(g.col)), (src, g.col)), shape=(n, n))
+    idx = np.flatnonzero(alive)
+    out = np.full(n, -1, dtype=np.int64)
+    if len(idx) == 0:
+        return out
+    D = shortest_path(A[idx][:, idx], unweighted=True, directed=False)
+    out[idx] = (D <= h).sum(axis=1) - 1
+    return out
+
+
+# ---------------------------------------------------------------- paper pins
+
+def test_fig1_core_h2_matches_example1(fig1):
+    g, vals = fig1
+    want = np.array([int(x) for x in vals["core_h2"]])
+    assert (oracle.peel(g, 2) == want).all()
+    assert (oracle.bruteforce(g, 2) == want).all()
+
+
+def test_fig1_core_h1_is_2_everywhere(fig1):
+    g, vals = fig1
+    want = np.array([int(x) for x in vals["core_h1"]])
+    assert (oracle.peel(g, 1) == want).all()
+    assert (oracle.kcore_bz(g) == want).all()
+
+
+def test_fig1_example2_hdegrees(fig1):
+    g, vals = fig1
+    d = oracle.hdegrees(g, 2)
+    v1 = 0
+    assert d[v1] == int(vals["hdeg2_v1"][0])
+    assert (d[1:] > d[v1]).all(), "v1 is the unique minimum"
+    alive = np.ones(g.n, np.uint8)
+    alive[v1] = 0
+    d1 = oracle.hdegrees(g, 2, alive)
+    for item in vals["after_v1_hdeg2"]:
+        v, want = item.split(":")
+        assert d1[int(v) - 1] == int(want)
+    # the ball of v1 is exactly {v2,v3,v4,v6}: deleting a ball vertex lowers
+    # d^2(v1), deleting anything else leaves it at 4
+    ball = {int(x) - 1 for x in vals["ball2_v1"]}
+    for u in range(1, g.n):
+        a = np.ones(g.n, np.uint8)
+        a[u] = 0
+        assert (oracle.hdegrees(g, 2, a)[v1] < 4) == (u in ball)
+
+
+def test_fig1_table1_ball_of_v5(fig1):
+    g, vals = fig1
+    alive = np.ones(g.n, np.uint8)
+    alive[[0, 1, 2]] = 0
+    ball = sorted(int(x) - 1 for x in vals["ball2_v5_after_v123"])
+    far = sorted(int(x) - 1 for x in vals["dist2_v5_after_v123"])
+    v5 = 4
+    assert oracle.hdegrees(g, 2, alive)[v5] == len(ball)
+    assert oracle.hdegrees(g, 1, alive)[v5] == len(ball) - len(far)
+    # exact membership: removing a ball vertex lowers d^2(v5) by at least one
+    for u in range(3, g.n):
+        if u == v5:
+            continue
+        a = alive.copy()
+        a[u] = 0
+        dropped = oracle.hdegrees(g, 2, a)[v5] < len(ball)
+        assert dropped == (u in ball)
+
+
+# ---------------------------------------------------------------- h-degrees
+
+@pytest.mark.parametrize("h", [1, 2, 3, 4, 6])
+def test_hdegrees_match_scipy_shortest_path(h):
+    for g in small_graphs(7, 9, (5, 60)):
+        assert (oracle.hdegrees(g, h) == scipy_hdeg(g, h)).all(), g.name
+
+
+@pytest.mark.parametrize("h", [1, 2, 3])
+def test_hdegrees_induced_subgraph_match_scipy(h):
+    rng = gg.Stream(11, "alive")
+    for g in small_graphs(8, 9, (5, 60)):
+        alive = (rng.uniform(g.n) < 0.7).astype(np.uint8)
+        got = oracle.hdegrees(g, h, alive)
+        want = scipy_hdeg(g, h, alive)
+        assert (got == want).all(), g.name
+
+
+def test_hdegrees_closed_forms():
+    for n in [1, 2, 5, 9]:
+        assert (oracle.hdegrees(gg.complete(n), 1) == n - 1).all()
+    for n in [3, 7]:
+        s = gg.star(n)
+        d1, d2 = oracle.hdegrees(s, 1), oracle.hdegrees(s, 2)
+        assert d1[0] == n - 1 and (d1[1:] == 1).all()
+        assert (d2 == n - 1).all()
+    for n in [5, 8, 11]:
+        for h in [1, 2, 3, 4, 6]:
+            assert (oracle.hdegrees(gg.cycle(n), h) == min(2 * h, n - 1)).all()
+            i = np.arange(n)
+            want = np.minimum(i, h) + np.minimum(n - 1 - i, h)
+            assert (oracle.hdegrees(gg.path(n), h) == want).all()
+    assert (oracle.hdegrees(gg.empty(6), 3) == 0).all()
+
+
+def test_hdegree_list_matches_full():
+    g = gg.chung_lu(3000, 8.0, 2.5, 200.0, 9)
+    v = np.array([0, 5, 17, 2999, 1234], dtype=np.int32)
+    for h in [1, 2, 3]:
+        assert (oracle.hdegree_list(g, h, v) == oracle.hdegrees(g, h)[v]).all()
+
+
+# ---------------------------------------------------------------- core index
+
+def test_core_closed_forms():
+    for n in [2, 4, 7]:
+        for h in [1, 2, 3]:
+            assert (oracle.peel(gg.complete(n), h) == n - 1).all()
+    for n in [4, 9]:
+        assert (oracle.peel(gg.star(n), 1) == 1).all()
+        for h in [2, 3]:
+            assert (oracle.peel(gg.star(n), h) == n - 1).all()
+    for n in [7, 10, 13]:
+        for h in [1, 2, 3]:
+            want = 2 * h if 2 * h < n else n - 1
+            assert (oracle.peel(gg.cycle(n), h) == want).all(), (n, h)
+    for n in [2, 6, 9]:
+        for h in [1, 2, 3]:
+            assert (oracle.peel(gg.path(n), h) == min(h, n - 1)).all(), (n, h)
+    for a, b in [(2, 3), (3, 5)]:
+        assert (oracle.peel(gg.complete_bipartite(a, b), 1) == min(a, b)).all()
+        assert (oracle.peel(gg.complete_bipartite(a, b), 2) == a + b - 1).all()
+    assert (oracle.peel(gg.empty(5), 2) == 0).all()
+
+
+def test_core_disjoint_union_is_per_component():
+    parts = [gg.cycle(9), gg.complete(4), gg.star(5), gg.erdos_renyi_gnm(30, 60, 3)]
+    u = gg.disjoint_union(*parts)
+    for h in [1, 2, 3]:
+        want = np.concatenate([oracle.peel(p, h) for p in parts])
+        assert (oracle.peel(u, h) == want).all()
+
+
+@pytest.mark.parametrize("h", [1, 2, 3, 4])
+def test_peel_matches_bruteforce_random(h):
+    for g in small_graphs(100 + h, 15, (3, 13)):
+        assert (oracle.peel(g, h) == oracle.bruteforce(g, h)).all(), g.name
+
+
+def test_peel_matches_bruteforce_all_graphs_n5():
+    n = 5
+    pairs = list(itertools.combinations(range(n), 2))
+    for mask in range(1 << len(pairs)):
+        e = [pairs[i] for i in range(len(pairs)) if mask >> i & 1]
+        g = gg.from_edge_list(n, e) if e else gg.empty(n)
+        for h in (1, 2, 3):
+            assert (oracle.peel(g, h) == oracle.bruteforce(g, h)).all(), (mask, h)
+
+
+def test_h1_equals_classic_kcore():
+    nx = pytest.importorskip("networkx")
+    for g in small_graphs(200, 9, (20, 400)) + [gg.chung_lu(2000, 10, 2.5, 300, 4)]:
+        c1 = oracle.peel(g, 1)
+        assert (c1 == oracle.kcore_bz(g)).all()
+        G = nx.Graph()
+        G.add_nodes_from(range(g.n))
+        G.add_edges_from(g.edges().tolist())
+        cn = nx.core_number(G)
+        assert all(cn[v] == c1[v] for v in range(g.n)), g.name
+
+
+def test_invariants_monotone_bounded_equivariant():
+    for g in small_graphs(300, 9, (10, 120)):
+        prev = None
+        for h in [1, 2, 3, 4]:
+            c = oracle.peel(g, h)
+            d = oracle.hdegrees(g, h)
+            assert (c <= d).all()
+            if prev is not None:
+                assert (c >= prev).all(), "core_h <= core_{h+1}"
+            prev = c
+        perm = np.argsort(gg.Stream(5, g.name).u64(g.n), kind="stable")
+        gp = gg.relabel(g, perm)
+        c2 = oracle.peel(g, 2)
+        assert (oracle.peel(gp, 2)[perm] == c2).all()
+
+
+def test_h_at_least_diameter_gives_component_size_minus_one():
+    from scipy.sparse.csgraph import connected_components
+    for g in small_graphs(400, 6, (5, 40)):
+        src = np.repeat(np.arange(g.n), g.degrees())
+        A = sp.csr_matrix((np.ones(len(g.col)), (src, g.col)), shape=(g.n, g.n))
+        _, lab = connected_components(A, directed=False)
+        size = np.bincount(lab)[lab]
+        assert (oracle.peel(g, g.n) == size - 1).all()
+
+
+# ---------------------------------------------------------------- certificate
+
+def test_certificate_accepts_true_and_rejects_mutations():
+    for g in small_graphs(500, 6, (10, 80)):
+        for h in [1, 2, 3]:
+            c = oracle.peel(g, h)
+            r = oracle.level_rounds(g, h, c)
+            fails, _ = oracle.certificate(g, h, c, r)
+            assert fails == 0, (g.name, h)
+            if g.n < 2:
+                continue
+            v = int(np.argmax(c))
+            for delta in (+1, -1):
+                c2 = c.copy()
+                c2[v] += delta
+                if c2[v] < 0:
+                    continue
+                assert oracle.certificate(g, h, c2, r)[0] > 0
+            # shifting the latest round earlier breaks it too
+            late = int(np.argmax(r))
+            if r[late] > 0 and (r == r[late]).sum() == 1 and (c == c[late]).sum() < g.n:
+                r2 = r.copy()
+                r2[late] = 0
+                c2 = c.copy()
+                assert oracle.certificate(g, h, c2, r2)[0] > 0
+
+
+def test_certificate_rejects_uniform_shift():
+    g = gg.erdos_renyi_gnm(60, 150, 12)
+    c = oracle.peel(g, 2)
+    r = oracle.level_rounds(g, 2, c)
+    assert oracle.certificate(g, 2, c + 1, r)[0] > 0
+    assert oracle.certificate(g, 2, np.maximum(c - 1, 0), r)[0] > 0
