@@ -364,3 +364,41 @@ def relabel(g: Graph, perm: np.ndarray) -> Graph:
 
 def empty(n: int) -> Graph:
     return Graph(n, np.zeros(n + 1, dtype=np.int32), np.zeros(0, dtype=np.int32), f"empty{n}")
+
+
+# ---------------------------------------------------------------------------
+# On-disk cache of generated graphs (generation of the 1e6-vertex graph takes
+# tens of seconds); keyed by the generator call, stored as .npz.
+# ---------------------------------------------------------------------------
+
+def cache_dir() -> str:
+    import os
+    d = os.environ.get("KHCORE_GRAPH_CACHE", os.path.join("/tmp", "khcore_graphs"))
+    os.makedirs(d, exist_ok=True)
+    return d
+
+
+def cached(key: str, make) -> Graph:
+    import os
+    path = os.path.join(cache_dir(), key + ".npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        return Graph(int(z["n"]), z["row_ptr"], z["col"], key)
+    g = make()
+    tmp = path + f".tmp{os.getpid()}.npz"
+    np.savez(tmp, n=g.n, row_ptr=g.row_ptr, col=g.col)
+    os.replace(tmp, path)
+    g.name = key
+    return g
+
+
+CONFIGS = {
+    "er2000": (config1_er, (2,)),
+    "cl1m": (config2_chung_lu, (2, 3)),
+    "rmat18": (config3_rmat, (4, 5)),
+}
+
+
+def config_graph(name: str) -> Graph:
+    make, _ = CONFIGS[name]
+    return cached(name, make)

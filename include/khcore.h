@@ -1,0 +1,152 @@
+/*
+ * khcore.h — C ABI of the GB300 (sm_103a) library for distance-generalized
+ * (k,h)-core decomposition ("Scaling Up Distance-generalized Core
+ * Decomposition", 2020).
+ *
+ * Model (Sec. II). G = (V, E) is undirected and unweighted. For h >= 1 the
+ * h-hop neighbourhood N_v^h(G) is the set of vertices u != v with
+ * dist_G(u, v) <= h, and the h-hop degree d_v^h(G) = |N_v^h(G)|. The
+ * (k,h)-core is the largest induced subgraph in which every vertex has
+ * h-hop degree >= k measured INSIDE that subgraph (Definition 2), and the
+ * core index core_h(v) is the largest k whose (k,h)-core contains v. The
+ * problem (end of Sec. II) is to compute core_h(v) for all v.
+ *
+ * Graph format. An int32 CSR over vertices 0..n-1: row_ptr has n+1 entries,
+ * row_ptr[0] = 0, non-decreasing, and col has row_ptr[n] entries with
+ * 0 <= col[e] < n. The graph is simple and undirected, so the CSR holds both
+ * directions of every edge, no self-loops and no duplicate entries. Row order
+ * does not matter.
+ *
+ * Pointers. Every array argument may be a host pointer (pageable or pinned)
+ * or a CUDA device pointer; the library tells them apart with
+ * cudaPointerGetAttributes. Output arrays are allocated by the caller.
+ * The library never keeps a caller pointer past the call that received it.
+ *
+ * Errors. Every entry point returns a khcore_status and never throws or
+ * aborts. After a failure khcore_last_error(ctx) holds a one-line message.
+ * A CUDA error leaves the context failed: later calls on it return
+ * KHCORE_ECUDA, and the context may only be destroyed.
+ *
+ * Threads and streams. A context belongs to one host thread at a time. All
+ * of its device work is ordered on the stream given to khcore_create. The
+ * calls return after their outputs are written (host outputs are complete;
+ * device outputs are complete when the call returns, because each call
+ * synchronises its stream before returning).
+ */
+#ifndef KHCORE_H
+#define KHCORE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct khcore_ctx khcore_ctx;
+
+typedef enum {
+    KHCORE_OK = 0,
+    KHCORE_EINVAL = 1,    /* bad argument or malformed graph */
+    KHCORE_ENOMEM = 2,    /* device or host allocation failed */
+    KHCORE_ECUDA = 3,     /* a CUDA call failed; the context is now failed */
+    KHCORE_ETIMEOUT = 4,  /* a bounded device-side wait ran out */
+    KHCORE_EBUSY = 5,     /* resource (slot or memory budget) not available now */
+    KHCORE_EINTERNAL = 6  /* a device-side consistency check failed */
+} khcore_status;
+
+/* Flags for khcore_create. */
+#define KHCORE_FLAG_TRUST_INPUT 0x1u  /* skip CSR validation (caller guarantees the format) */
+
+/* Per-call statistics of khcore_decompose_ex. */
+typedef struct {
+    int32_t h;                 /* h actually used: min(h, max(n-1, 1)) */
+    int32_t rounds;            /* peel rounds (level-synchronous deletions) */
+    int32_t k_max;             /* largest core index */
+    int32_t words_per_vertex;  /* W: 64-bit words per vertex per source batch */
+    int64_t deleted_total;     /* sum over rounds of |D| (equals n) */
+    int64_t affected_total;    /* sum over rounds of |A| (vertices recomputed) */
+    int64_t source_batches;    /* multi-source BFS batches run, initial pass included */
+    int64_t kernel_launches;   /* kernels launched by this call */
+    double device_ms;          /* device time of the call (CUDA events) */
+} khcore_stats;
+
+/*
+ * khcore_create — copy an undirected graph to the device and set up the
+ * per-graph state (alive bitset, h-degrees, core indices, BFS bitsets).
+ *   n        number of vertices, n >= 0 (n = 0 is valid and gives empty results)
+ *   row_ptr  int32[n+1] CSR offsets (host or device)
+ *   col      int32[row_ptr[n]] neighbour ids (host or device; may be NULL if
+ *            row_ptr[n] == 0)
+ *   flags    KHCORE_FLAG_* bits
+ *   stream   cudaStream_t to order all work on, or NULL for a stream owned by
+ *            the context
+ *   out      receives the new context (NULL on failure)
+ * Returns KHCORE_EINVAL (with a message in khcore_last_error(NULL)) when the
+ * CSR is malformed: offsets not starting at 0 or decreasing, an id outside
+ * [0, n), a self-loop, a duplicate entry, or an edge present in one direction
+ * only. Returns KHCORE_ENOMEM if the device cannot hold the graph.
+ */
+khcore_status khcore_create(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                            uint32_t flags, void *stream, khcore_ctx **out);
+
+/*
+ * khcore_hdegrees — d_v^h(G) for every vertex of the whole graph (Sec. II;
+ * the first step of the peeling algorithms, Algorithm 1 and Algorithm 2).
+ *   h        hop bound, h >= 1 (EINVAL otherwise); h > n-1 acts as n-1
+ *   deg_out  int32[n], host or device; deg_out[v] = d_v^h(G)
+ * Computed by a multi-source h-bounded BFS on 64-bit source bitsets.
+ */
+khcore_status khcore_hdegrees(khcore_ctx *ctx, int32_t h, int32_t *deg_out);
+
+/*
+ * khcore_decompose — core_h(v) for every vertex (problem statement, Sec. II).
+ *   h         hop bound, h >= 1 (EINVAL otherwise); h > n-1 acts as n-1
+ *   core_out  int32[n], host or device
+ * Peels level-synchronously: at level k every alive vertex with h-degree
+ * <= k is deleted with core index k (Algorithm 1 deletes them one at a time
+ * in some order; the result is the same, because h-degrees only fall as
+ * vertices go). Only alive vertices within h hops of the deleted set can
+ * change h-degree (Sec. IV-A, Observation 1); their h-degrees are recomputed
+ * on the surviving induced subgraph.
+ */
+khcore_status khcore_decompose(khcore_ctx *ctx, int32_t h, int32_t *core_out);
+
+/*
+ * khcore_decompose_ex — khcore_decompose with the peel round of every vertex
+ * and statistics.
+ *   round_out  int32[n] or NULL; round_out[v] = the round in which v was
+ *              deleted (0-based). Rounds and core indices together form a
+ *              certificate that a CPU checker can verify.
+ *   stats      khcore_stats* or NULL
+ */
+khcore_status khcore_decompose_ex(khcore_ctx *ctx, int32_t h, int32_t *core_out,
+                                  int32_t *round_out, khcore_stats *stats);
+
+/* Number of vertices and directed CSR entries of the context's graph. */
+int32_t khcore_num_vertices(const khcore_ctx *ctx);
+int64_t khcore_num_entries(const khcore_ctx *ctx);
+
+/*
+ * khcore_set_words — choose W, the number of 64-bit source words per vertex
+ * (64*W sources per BFS batch). W must be 1, 2, 4, 8 or 16 (EINVAL
+ * otherwise); 0 restores the automatic choice. Results do not depend on W.
+ */
+khcore_status khcore_set_words(khcore_ctx *ctx, int32_t words);
+
+/* Release every device and host resource of the context. NULL is a no-op. */
+void khcore_destroy(khcore_ctx *ctx);
+
+/* Message of the last failure on ctx (or of the last failed khcore_create
+ * when ctx is NULL); "" if none. The pointer stays valid until the next call
+ * on the same context. */
+const char *khcore_last_error(const khcore_ctx *ctx);
+
+/* Static name of a status code. */
+const char *khcore_status_string(khcore_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KHCORE_H */

@@ -1,0 +1,247 @@
+"""GB300 (sm_103a) library for distance-generalized (k,h)-core decomposition.
+
+A thin ctypes binding over the C ABI in include/khcore.h. The binding only
+marshals arguments: every step of the computation runs in the library's CUDA
+kernels (libkhcore.so, built by paper_2006_03372_gb300._build). There is no
+CPU fallback: if the library is missing or no GPU is present the calls raise.
+
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA
+memory); the C library tells host and device pointers apart itself.
+
+    ctx = khcore_create(n, row_ptr, col)          # int32 CSR, both directions
+    deg = khcore_hdegrees(ctx, h)                 # d_v^h(G) for all v   (Sec. II)
+    core = khcore_decompose(ctx, h)               # core_h(v) for all v  (Sec. II)
+    core, rnd, stats = khcore_decompose_ex(ctx, h)
+    khcore_destroy(ctx)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from ._build import LIB as _LIB_PATH
+from ._build import build as _build_lib
+
+__all__ = [
+    "KHCoreError", "khcore_create", "khcore_hdegrees", "khcore_decompose", "khcore_decompose_ex",
+    "khcore_destroy", "khcore_last_error", "khcore_set_words", "khcore_status_string", "Stats",
+    "KHCore", "library_path", "load_library",
+]
+
+STATUS = {0: "KHCORE_OK", 1: "KHCORE_EINVAL", 2: "KHCORE_ENOMEM", 3: "KHCORE_ECUDA",
+          4: "KHCORE_ETIMEOUT", 5: "KHCORE_EBUSY", 6: "KHCORE_EINTERNAL"}
+FLAG_TRUST_INPUT = 0x1
+
+
+class KHCoreError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_int32), ("rounds", ctypes.c_int32), ("k_max", ctypes.c_int32),
+                ("words_per_vertex", ctypes.c_int32), ("deleted_total", ctypes.c_int64),
+                ("affected_total", ctypes.c_int64), ("source_batches", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("device_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load_library(build_if_missing: bool = False):
+    """Load libkhcore.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            if not build_if_missing:
+                raise ImportError(
+                    f"libkhcore.so is not built ({_LIB_PATH}); run __graft_entry__.build() or "
+                    "python -m paper_2006_03372_gb300._build")
+            _build_lib()
+        lib = ctypes.CDLL(_LIB_PATH)
+        P, i32, u32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64
+        lib.khcore_create.argtypes = [i32, P, P, u32, P, ctypes.POINTER(P)]
+        lib.khcore_create.restype = ctypes.c_int
+        lib.khcore_hdegrees.argtypes = [P, i32, P]
+        lib.khcore_hdegrees.restype = ctypes.c_int
+        lib.khcore_decompose.argtypes = [P, i32, P]
+        lib.khcore_decompose.restype = ctypes.c_int
+        lib.khcore_decompose_ex.argtypes = [P, i32, P, P, ctypes.POINTER(Stats)]
+        lib.khcore_decompose_ex.restype = ctypes.c_int
+        lib.khcore_destroy.argtypes = [P]
+        lib.khcore_destroy.restype = None
+        lib.khcore_last_error.argtypes = [P]
+        lib.khcore_last_error.restype = ctypes.c_char_p
+        lib.khcore_status_string.argtypes = [ctypes.c_int]
+        lib.khcore_status_string.restype = ctypes.c_char_p
+        lib.khcore_set_words.argtypes = [P, i32]
+        lib.khcore_set_words.restype = ctypes.c_int
+        lib.khcore_num_vertices.argtypes = [P]
+        lib.khcore_num_vertices.restype = i32
+        lib.khcore_num_entries.argtypes = [P]
+        lib.khcore_num_entries.restype = i64
+        _lib = lib
+        return lib
+
+
+# ---------------------------------------------------------------- marshalling
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, dtype=np.int32):
+    """(pointer, keepalive) for a numpy array or torch tensor of int32."""
+    if a is None:
+        return None, None
+    if _is_torch(a):
+        import torch
+        if a.dtype != torch.int32:
+            raise TypeError("expected an int32 tensor")
+        if not a.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return ctypes.c_void_p(a.data_ptr() if a.numel() else 0), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data_as(ctypes.c_void_p), arr
+
+
+def _check(lib, ctx, status):
+    if status != 0:
+        msg = lib.khcore_last_error(ctx)
+        raise KHCoreError(status, msg.decode() if msg else "")
+
+
+class _Ctx(ctypes.c_void_p):
+    pass
+
+
+def khcore_create(n: int, row_ptr, col, flags: int = 0, stream=None):
+    """Copy an undirected int32 CSR to the device; returns an opaque context.
+    stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None."""
+    lib = load_library()
+    rp, k1 = _ptr(row_ptr)
+    cl, k2 = _ptr(col)
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    out = ctypes.c_void_p()
+    st = lib.khcore_create(int(n), rp, cl, int(flags), ctypes.c_void_p(stream) if stream else None,
+                           ctypes.byref(out))
+    _check(lib, None, st)
+    del k1, k2
+    return _Ctx(out.value)
+
+
+def khcore_destroy(ctx) -> None:
+    if ctx is not None and ctx.value:
+        load_library().khcore_destroy(ctx)
+        ctx.value = None
+
+
+def khcore_last_error(ctx=None) -> str:
+    m = load_library().khcore_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def khcore_status_string(status: int) -> str:
+    return load_library().khcore_status_string(int(status)).decode()
+
+
+def khcore_set_words(ctx, words: int) -> None:
+    lib = load_library()
+    _check(lib, ctx, lib.khcore_set_words(ctx, int(words)))
+
+
+def _out(ctx, out):
+    n = load_library().khcore_num_vertices(ctx)
+    if out is None:
+        out = np.empty(n, dtype=np.int32)
+    elif len(out) != n:
+        raise ValueError(f"output has {len(out)} entries, graph has {n} vertices")
+    if isinstance(out, np.ndarray) and (out.dtype != np.int32 or not out.flags["C_CONTIGUOUS"]):
+        raise TypeError("output must be a contiguous int32 array")
+    return out
+
+
+def khcore_hdegrees(ctx, h: int, deg_out=None):
+    """d_v^h(G) for all v; writes deg_out (host or device) if given."""
+    lib = load_library()
+    out = _out(ctx, deg_out)
+    p, _ = _ptr(out)
+    _check(lib, ctx, lib.khcore_hdegrees(ctx, int(h), p))
+    return out
+
+
+def khcore_decompose(ctx, h: int, core_out=None):
+    """core_h(v) for all v."""
+    lib = load_library()
+    out = _out(ctx, core_out)
+    p, _ = _ptr(out)
+    _check(lib, ctx, lib.khcore_decompose(ctx, int(h), p))
+    return out
+
+
+def khcore_decompose_ex(ctx, h: int, core_out=None, round_out=None, want_rounds: bool = True):
+    """(core, round, stats): core index, peel round of every vertex, statistics."""
+    lib = load_library()
+    core = _out(ctx, core_out)
+    rnd = _out(ctx, round_out) if (want_rounds or round_out is not None) else None
+    pc, _ = _ptr(core)
+    pr, _ = _ptr(rnd)
+    stats = Stats()
+    _check(lib, ctx, lib.khcore_decompose_ex(ctx, int(h), pc, pr, ctypes.byref(stats)))
+    return core, rnd, stats.as_dict()
+
+
+class KHCore:
+    """Context manager around one device-resident graph."""
+
+    def __init__(self, n, row_ptr, col, flags: int = 0, stream=None, words: int = 0):
+        self.ctx = khcore_create(n, row_ptr, col, flags, stream)
+        self.n = int(n)
+        if words:
+            khcore_set_words(self.ctx, words)
+
+    @classmethod
+    def from_graph(cls, g, **kw):
+        return cls(g.n, g.row_ptr, g.col, **kw)
+
+    def hdegrees(self, h, out=None):
+        return khcore_hdegrees(self.ctx, h, out)
+
+    def decompose(self, h, out=None):
+        return khcore_decompose(self.ctx, h, out)
+
+    def decompose_ex(self, h, core_out=None, round_out=None):
+        return khcore_decompose_ex(self.ctx, h, core_out, round_out)
+
+    def set_words(self, w):
+        khcore_set_words(self.ctx, w)
+
+    def close(self):
+        khcore_destroy(self.ctx)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,533 @@
+// khcore_api.cu — the C ABI declared in include/khcore.h: context life cycle,
+// CSR validation, and the host side of the level-synchronous peeler.
+#include <algorithm>
+#include <climits>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/khcore.h"
+#include "khcore_internal.cuh"
+
+using namespace khc;
+
+struct khcore_ctx {
+    int32_t n = 0;
+    int64_t m = 0;
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    bool failed = false;
+    std::string err;
+
+    // graph (device)
+    int32_t *row_ptr = nullptr, *col = nullptr;
+    int32_t *classes = nullptr;  // light | medium | heavy lists, back to back
+    int32_t n_light = 0, n_medium = 0, n_heavy = 0;
+
+    // peel state (device)
+    uint32_t *alive = nullptr;
+    int32_t *deg = nullptr, *core = nullptr, *rnd = nullptr, *src = nullptr;
+    uint32_t *aff[2] = {nullptr, nullptr};
+    uint32_t *vis = nullptr;
+    PeelState *st = nullptr;
+    PeelState *st_host = nullptr;  // pinned mirror
+
+    // BFS buffers, sized for W_alloc words per vertex
+    int W_req = 0;  // 0 = automatic
+    int W_alloc = 0;
+    uint64_t *V = nullptr, *F[2] = {nullptr, nullptr};
+    uint8_t *flag[2] = {nullptr, nullptr};
+    int32_t *cnt = nullptr;
+
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+    GraphView view() const
+    {
+        GraphView g;
+        g.n = n;
+        g.m = m;
+        g.row_ptr = row_ptr;
+        g.col = col;
+        g.light = classes;
+        g.medium = classes + n_light;
+        g.heavy = classes + n_light + n_medium;
+        g.n_light = n_light;
+        g.n_medium = n_medium;
+        g.n_heavy = n_heavy;
+        return g;
+    }
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+khcore_status fail(khcore_ctx *c, khcore_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) {
+        c->err = buf;
+        if (s == KHCORE_ECUDA) c->failed = true;
+    } else {
+        g_create_err = buf;
+    }
+    return s;
+}
+
+#define CU(call)                                                                            \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            if (e_ == cudaErrorMemoryAllocation) {                                          \
+                (void)cudaGetLastError();                                                   \
+                return fail(c, KHCORE_ENOMEM, "%s: %s", #call, cudaGetErrorString(e_));     \
+            }                                                                               \
+            return fail(c, KHCORE_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));          \
+        }                                                                                   \
+    } while (0)
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+cudaError_t dev_alloc(T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void **)p, count * sizeof(T));
+}
+
+// Copy `count` elements from a host or device pointer into a host vector.
+template <class T>
+cudaError_t fetch(std::vector<T> &dst, const T *src, size_t count)
+{
+    dst.resize(count);
+    if (count == 0) return cudaSuccess;
+    if (is_device_ptr(src)) return cudaMemcpy(dst.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost);
+    std::memcpy(dst.data(), src, count * sizeof(T));
+    return cudaSuccess;
+}
+
+// Validates an undirected simple CSR; on success `sorted` holds col with every
+// row sorted (the library does not depend on row order, but validation does).
+bool validate_csr(int32_t n, const std::vector<int32_t> &rp, const std::vector<int32_t> &col,
+                  std::vector<int32_t> &sorted, std::string &msg)
+{
+    char buf[256];
+    if (rp[0] != 0) {
+        msg = "row_ptr[0] must be 0";
+        return false;
+    }
+    for (int32_t v = 0; v < n; v++)
+        if (rp[v + 1] < rp[v]) {
+            snprintf(buf, sizeof buf, "row_ptr decreases at vertex %d", v);
+            msg = buf;
+            return false;
+        }
+    sorted = col;
+    for (int32_t v = 0; v < n; v++) {
+        auto b = sorted.begin() + rp[v], e = sorted.begin() + rp[v + 1];
+        if (!std::is_sorted(b, e)) std::sort(b, e);
+        for (auto it = b; it != e; ++it) {
+            const int32_t u = *it;
+            if (u < 0 || u >= n) {
+                snprintf(buf, sizeof buf, "neighbour id %d of vertex %d outside [0, %d)", u, v, n);
+                msg = buf;
+                return false;
+            }
+            if (u == v) {
+                snprintf(buf, sizeof buf, "self-loop at vertex %d", v);
+                msg = buf;
+                return false;
+            }
+            if (it != b && *(it - 1) == u) {
+                snprintf(buf, sizeof buf, "duplicate edge %d-%d", v, u);
+                msg = buf;
+                return false;
+            }
+        }
+    }
+    for (int32_t v = 0; v < n; v++)
+        for (int32_t e = rp[v]; e < rp[v + 1]; e++) {
+            const int32_t u = sorted[e];
+            if (!std::binary_search(sorted.begin() + rp[u], sorted.begin() + rp[u + 1], v)) {
+                snprintf(buf, sizeof buf, "edge %d-%d has no reverse entry (graph must be undirected)", v, u);
+                msg = buf;
+                return false;
+            }
+        }
+    return true;
+}
+
+int auto_words(int32_t n)
+{
+    // 64*W sources per batch; keep one frontier array (n*W*8 bytes) near
+    // 32 MB so that the neighbour gathers stay in L2, with W in [4, 16]
+    // (W >= 4 makes each gather a whole 32-byte sector).
+    if (n <= 64) return 1;
+    if (n <= 128) return 2;
+    if (n <= 256) return 4;
+    int64_t w = (int64_t)(32ll << 20) / ((int64_t)n * 8);
+    int W = 4;
+    while (W < 16 && 2 * W <= w) W *= 2;
+    return W;
+}
+
+khcore_status ensure_bfs(khcore_ctx *c, int W)
+{
+    if (c->W_alloc == W) return KHCORE_OK;
+    cudaFree(c->V);
+    cudaFree(c->F[0]);
+    cudaFree(c->F[1]);
+    cudaFree(c->cnt);
+    c->V = c->F[0] = c->F[1] = nullptr;
+    c->cnt = nullptr;
+    c->W_alloc = 0;
+    const size_t words = (size_t)std::max(c->n, 1) * W;
+    CU(dev_alloc(&c->V, words));
+    CU(dev_alloc(&c->F[0], words));
+    CU(dev_alloc(&c->F[1], words));
+    CU(dev_alloc(&c->cnt, (size_t)64 * W));
+    CU(cudaMemsetAsync(c->V, 0, words * sizeof(uint64_t), c->stream));
+    CU(cudaMemsetAsync(c->cnt, 0, (size_t)64 * W * sizeof(int32_t), c->stream));
+    c->W_alloc = W;
+    return KHCORE_OK;
+}
+
+int bfs_grid(khcore_ctx *c, int W) { return c->sm_count * max_blocks_per_sm_bfs(W); }
+
+// h-degrees of the sources src[0..ns) in G[alive], in batches of 64*W.
+khcore_status hdeg_sources(khcore_ctx *c, int W, int32_t h, int32_t ns, int64_t *batches,
+                           int64_t *launches)
+{
+    const GraphView g = c->view();
+    BfsBufs b;
+    b.V = c->V;
+    b.F[0] = c->F[0];
+    b.F[1] = c->F[1];
+    b.flag[0] = c->flag[0];
+    b.flag[1] = c->flag[1];
+    b.cnt = c->cnt;
+    const int32_t S = 64 * W;
+    const int grid = bfs_grid(c, W);
+    for (int32_t off = 0; off < ns; off += S) {
+        const int32_t cur = std::min(S, ns - off);
+        CU(run_bfs_batch(W, g, c->alive, b, c->src + off, cur, h, c->deg, grid, c->stream, launches));
+        if (batches) ++*batches;
+    }
+    return KHCORE_OK;
+}
+
+khcore_status check_ctx(khcore_ctx *c)
+{
+    if (!c) return KHCORE_EINVAL;
+    if (c->failed) return KHCORE_ECUDA;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return fail(c, KHCORE_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    return KHCORE_OK;
+}
+
+khcore_status write_out(khcore_ctx *c, int32_t *dst, const int32_t *src_dev)
+{
+    if (!dst || c->n == 0) return KHCORE_OK;
+    const size_t bytes = (size_t)c->n * sizeof(int32_t);
+    CU(cudaMemcpyAsync(dst, src_dev, bytes, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       c->stream));
+    return KHCORE_OK;
+}
+
+int32_t effective_h(int32_t n, int32_t h) { return std::min(h, std::max(n - 1, 1)); }
+
+}  // namespace
+
+extern "C" {
+
+const char *khcore_status_string(khcore_status s)
+{
+    switch (s) {
+    case KHCORE_OK: return "KHCORE_OK";
+    case KHCORE_EINVAL: return "KHCORE_EINVAL";
+    case KHCORE_ENOMEM: return "KHCORE_ENOMEM";
+    case KHCORE_ECUDA: return "KHCORE_ECUDA";
+    case KHCORE_ETIMEOUT: return "KHCORE_ETIMEOUT";
+    case KHCORE_EBUSY: return "KHCORE_EBUSY";
+    case KHCORE_EINTERNAL: return "KHCORE_EINTERNAL";
+    }
+    return "KHCORE_UNKNOWN";
+}
+
+const char *khcore_last_error(const khcore_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
+
+int32_t khcore_num_vertices(const khcore_ctx *ctx) { return ctx ? ctx->n : 0; }
+int64_t khcore_num_entries(const khcore_ctx *ctx) { return ctx ? ctx->m : 0; }
+
+void khcore_destroy(khcore_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream && !c->failed) cudaStreamSynchronize(c->stream);
+    cudaFree(c->row_ptr);
+    cudaFree(c->col);
+    cudaFree(c->classes);
+    cudaFree(c->alive);
+    cudaFree(c->deg);
+    cudaFree(c->core);
+    cudaFree(c->rnd);
+    cudaFree(c->src);
+    cudaFree(c->aff[0]);
+    cudaFree(c->aff[1]);
+    cudaFree(c->vis);
+    cudaFree(c->st);
+    cudaFree(c->V);
+    cudaFree(c->F[0]);
+    cudaFree(c->F[1]);
+    cudaFree(c->flag[0]);
+    cudaFree(c->flag[1]);
+    cudaFree(c->cnt);
+    if (c->st_host) cudaFreeHost(c->st_host);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    (void)cudaGetLastError();
+    delete c;
+}
+
+khcore_status khcore_create(int32_t n, const int32_t *row_ptr, const int32_t *col, uint32_t flags, void *stream,
+                            khcore_ctx **out)
+{
+    khcore_ctx *c = nullptr;
+    if (!out) return fail(nullptr, KHCORE_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 0) return fail(nullptr, KHCORE_EINVAL, "n must be >= 0 (got %d)", n);
+    if (!row_ptr) return fail(nullptr, KHCORE_EINVAL, "row_ptr is NULL");
+
+    std::vector<int32_t> rp, cl, sorted;
+    if (fetch(rp, row_ptr, (size_t)n + 1) != cudaSuccess)
+        return fail(nullptr, KHCORE_ECUDA, "cannot read row_ptr");
+    const int64_t m = rp[n];
+    if (m < 0) return fail(nullptr, KHCORE_EINVAL, "row_ptr[n] is negative");
+    if (m > 0 && !col) return fail(nullptr, KHCORE_EINVAL, "col is NULL but row_ptr[n] = %lld", (long long)m);
+    if (fetch(cl, col, (size_t)m) != cudaSuccess) return fail(nullptr, KHCORE_ECUDA, "cannot read col");
+    if (!(flags & KHCORE_FLAG_TRUST_INPUT)) {
+        std::string msg;
+        if (!validate_csr(n, rp, cl, sorted, msg)) return fail(nullptr, KHCORE_EINVAL, "invalid CSR: %s", msg.c_str());
+    } else {
+        sorted.swap(cl);
+    }
+
+    c = new (std::nothrow) khcore_ctx();
+    if (!c) return fail(nullptr, KHCORE_ENOMEM, "host allocation failed");
+    c->n = n;
+    c->m = m;
+    khcore_status st = KHCORE_OK;
+    do {
+        cudaError_t e = cudaGetDevice(&c->device);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+        if (e != cudaSuccess) {
+            st = fail(nullptr, KHCORE_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+            break;
+        }
+        if (stream) {
+            c->stream = (cudaStream_t)stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) {
+                st = fail(nullptr, KHCORE_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+                break;
+            }
+            c->own_stream = true;
+        }
+        // degree classes
+        std::vector<int32_t> classes;
+        classes.reserve(n);
+        for (int pass = 0; pass < 3; pass++)
+            for (int32_t v = 0; v < n; v++) {
+                const int32_t d = rp[v + 1] - rp[v];
+                const int cls = d <= kLightMax ? 0 : (d <= kMediumMax ? 1 : 2);
+                if (cls == pass) classes.push_back(v);
+            }
+        for (int32_t v = 0; v < n; v++) {
+            const int32_t d = rp[v + 1] - rp[v];
+            if (d <= kLightMax) c->n_light++;
+            else if (d <= kMediumMax) c->n_medium++;
+            else c->n_heavy++;
+        }
+        const size_t nw = ((size_t)n + 31) / 32;
+        auto A = [&](cudaError_t e2) {
+            if (e2 != cudaSuccess && st == KHCORE_OK) {
+                (void)cudaGetLastError();
+                st = fail(nullptr, e2 == cudaErrorMemoryAllocation ? KHCORE_ENOMEM : KHCORE_ECUDA,
+                          "device allocation: %s", cudaGetErrorString(e2));
+            }
+        };
+        A(dev_alloc(&c->row_ptr, (size_t)n + 1));
+        A(dev_alloc(&c->col, (size_t)m));
+        A(dev_alloc(&c->classes, (size_t)n));
+        A(dev_alloc(&c->alive, nw));
+        A(dev_alloc(&c->deg, (size_t)n));
+        A(dev_alloc(&c->core, (size_t)n));
+        A(dev_alloc(&c->rnd, (size_t)n));
+        A(dev_alloc(&c->src, (size_t)n));
+        A(dev_alloc(&c->aff[0], nw));
+        A(dev_alloc(&c->aff[1], nw));
+        A(dev_alloc(&c->vis, nw));
+        A(dev_alloc(&c->st, 1));
+        A(dev_alloc(&c->flag[0], (size_t)n));
+        A(dev_alloc(&c->flag[1], (size_t)n));
+        if (st != KHCORE_OK) break;
+        e = cudaMallocHost((void **)&c->st_host, sizeof(PeelState));
+        if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+        if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->row_ptr, rp.data(), ((size_t)n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                c->stream);
+        if (e == cudaSuccess && m)
+            e = cudaMemcpyAsync(c->col, sorted.data(), (size_t)m * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess && n)
+            e = cudaMemcpyAsync(c->classes, classes.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            st = fail(nullptr, KHCORE_ECUDA, "graph upload: %s", cudaGetErrorString(e));
+            break;
+        }
+    } while (0);
+    if (st != KHCORE_OK) {
+        khcore_destroy(c);
+        return st;
+    }
+    *out = c;
+    return KHCORE_OK;
+}
+
+khcore_status khcore_set_words(khcore_ctx *c, int32_t words)
+{
+    if (!c) return KHCORE_EINVAL;
+    if (words != 0 && words != 1 && words != 2 && words != 4 && words != 8 && words != 16)
+        return fail(c, KHCORE_EINVAL, "words must be 0, 1, 2, 4, 8 or 16 (got %d)", words);
+    c->W_req = words;
+    return KHCORE_OK;
+}
+
+khcore_status khcore_hdegrees(khcore_ctx *c, int32_t h, int32_t *deg_out)
+{
+    khcore_status s = check_ctx(c);
+    if (s != KHCORE_OK) return s;
+    if (h < 1) return fail(c, KHCORE_EINVAL, "h must be >= 1 (got %d)", h);
+    if (!deg_out && c->n) return fail(c, KHCORE_EINVAL, "deg_out is NULL");
+    if (c->n == 0) return KHCORE_OK;
+    const int W = c->W_req ? c->W_req : auto_words(c->n);
+    if ((s = ensure_bfs(c, W)) != KHCORE_OK) return s;
+    const int32_t he = effective_h(c->n, h);
+    CU(launch_alive_init(c->alive, c->n, c->stream));
+    CU(launch_iota(c->src, c->n, c->stream));
+    if ((s = hdeg_sources(c, W, he, c->n, nullptr, nullptr)) != KHCORE_OK) return s;
+    if ((s = write_out(c, deg_out, c->deg)) != KHCORE_OK) return s;
+    CU(cudaStreamSynchronize(c->stream));
+    return KHCORE_OK;
+}
+
+khcore_status khcore_decompose_ex(khcore_ctx *c, int32_t h, int32_t *core_out, int32_t *round_out,
+                                  khcore_stats *stats)
+{
+    khcore_status s = check_ctx(c);
+    if (s != KHCORE_OK) return s;
+    if (h < 1) return fail(c, KHCORE_EINVAL, "h must be >= 1 (got %d)", h);
+    if (!core_out && c->n) return fail(c, KHCORE_EINVAL, "core_out is NULL");
+    khcore_stats stt;
+    std::memset(&stt, 0, sizeof stt);
+    const int32_t he = c->n ? effective_h(c->n, h) : h;
+    stt.h = he;
+    if (c->n == 0) {
+        if (stats) *stats = stt;
+        return KHCORE_OK;
+    }
+    const int W = c->W_req ? c->W_req : auto_words(c->n);
+    stt.words_per_vertex = W;
+    if ((s = ensure_bfs(c, W)) != KHCORE_OK) return s;
+    const GraphView g = c->view();
+    const int grid = bfs_grid(c, W);
+    const size_t nwb = (((size_t)c->n + 31) / 32) * sizeof(uint32_t);
+
+    CU(cudaEventRecord(c->ev0, c->stream));
+    // initial state: everything alive, k = 0, all h-degrees
+    PeelState init;
+    std::memset(&init, 0, sizeof init);
+    init.min_deg = INT_MAX;
+    init.alive = c->n;
+    *c->st_host = init;
+    CU(cudaMemcpyAsync(c->st, c->st_host, sizeof(PeelState), cudaMemcpyHostToDevice, c->stream));
+    CU(launch_alive_init(c->alive, c->n, c->stream));
+    CU(launch_iota(c->src, c->n, c->stream));
+    stt.kernel_launches += 2;
+    if ((s = hdeg_sources(c, W, he, c->n, &stt.source_batches, &stt.kernel_launches)) != KHCORE_OK) return s;
+
+    int32_t round = 0;
+    for (;;) {
+        // one round: level, peel set D, affected set A, recompute deg[A]
+        CU(launch_min_alive_deg(g, c->alive, c->deg, c->st, grid, c->stream));
+        CU(launch_set_level(c->st, c->stream));
+        CU(cudaMemsetAsync(c->aff[0], 0, nwb, c->stream));
+        CU(cudaMemsetAsync(c->vis, 0, nwb, c->stream));
+        CU(launch_peel_compact(g, c->alive, c->deg, c->st, c->core, c->rnd, c->aff[0], grid, c->stream));
+        stt.kernel_launches += 3;
+        for (int lvl = 0; lvl < he; lvl++) {
+            CU(cudaMemsetAsync(c->aff[(lvl + 1) & 1], 0, nwb, c->stream));
+            CU(launch_affected_level(g, c->alive, c->aff[lvl & 1], c->aff[(lvl + 1) & 1], c->vis, grid, c->stream));
+            stt.kernel_launches++;
+        }
+        CU(launch_compact_affected(g, c->alive, c->vis, c->st, c->src, grid, c->stream));
+        stt.kernel_launches++;
+        CU(cudaMemcpyAsync(c->st_host, c->st, sizeof(PeelState), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        const PeelState ps = *c->st_host;
+        if (ps.nD <= 0)
+            return fail(c, KHCORE_EINTERNAL, "round %d deleted no vertex with %d alive", round, ps.alive);
+        stt.deleted_total += ps.nD;
+        stt.affected_total += ps.nA;
+        stt.k_max = ps.k;
+        round++;
+        if (ps.alive == 0) break;
+        if (ps.nA > 0 &&
+            (s = hdeg_sources(c, W, he, ps.nA, &stt.source_batches, &stt.kernel_launches)) != KHCORE_OK)
+            return s;
+        // advance the device-side round counter
+        c->st_host->round = round;
+        CU(cudaMemcpyAsync(&c->st->round, &c->st_host->round, sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    }
+    stt.rounds = round;
+    CU(cudaEventRecord(c->ev1, c->stream));
+    if ((s = write_out(c, core_out, c->core)) != KHCORE_OK) return s;
+    if ((s = write_out(c, round_out, c->rnd)) != KHCORE_OK) return s;
+    CU(cudaStreamSynchronize(c->stream));
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    stt.device_ms = ms;
+    if (stats) *stats = stt;
+    return KHCORE_OK;
+}
+
+khcore_status khcore_decompose(khcore_ctx *c, int32_t h, int32_t *core_out)
+{
+    return khcore_decompose_ex(c, h, core_out, nullptr, nullptr);
+}
+
+}  // extern "C"

@@ -1,0 +1,85 @@
+"""The C-ABI boundary on the CPU: the library builds for sm_103a, loads, and
+exports every entry point include/khcore.h declares; host-side argument and
+CSR validation returns KHCORE_EINVAL before any device work."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(khcore_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2006_03372_gb300 as kh
+    from paper_2006_03372_gb300 import _build
+    _build.build()
+    return kh.load_library()
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for s in ["khcore_create", "khcore_hdegrees", "khcore_decompose", "khcore_decompose_ex",
+              "khcore_destroy", "khcore_last_error"]:
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for s in declared_symbols():
+        assert hasattr(lib, s), f"{s} declared in include/ but not exported"
+
+
+def test_status_strings(lib):
+    import paper_2006_03372_gb300 as kh
+    for code, name in kh.STATUS.items():
+        assert kh.khcore_status_string(code) == name
+
+
+def _create_status(n, rp, col):
+    import paper_2006_03372_gb300 as kh
+    try:
+        ctx = kh.khcore_create(n, rp, col)
+    except kh.KHCoreError as e:
+        return e.status, str(e)
+    kh.khcore_destroy(ctx)
+    return 0, ""
+
+
+@pytest.mark.parametrize("case", ["selfloop", "dup", "asym", "range", "rowptr", "neg_n"])
+def test_malformed_csr_is_einval(lib, case):
+    g = gg.cycle(6)
+    rp, col, n = g.row_ptr.copy(), g.col.copy(), g.n
+    if case == "selfloop":
+        col[0] = 0
+    elif case == "dup":
+        col[1] = col[0]
+    elif case == "asym":
+        # drop one direction of edge 0-1 by rewiring 0's entry to 3
+        col[np.flatnonzero(col[rp[0]:rp[1]] == 1)[0]] = 3
+    elif case == "range":
+        col[2] = 99
+    elif case == "rowptr":
+        rp[3] = rp[2] - 1
+    elif case == "neg_n":
+        n = -1
+    st, msg = _create_status(n, rp, col)
+    assert st == 1, msg
+
+
+def test_compiled_for_sm_103a_only():
+    from paper_2006_03372_gb300 import _build
+    assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]

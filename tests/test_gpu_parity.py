@@ -1,0 +1,147 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle,
+element by element, bit-exact (integer results)."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from conftest import small_graphs
+
+pytestmark = pytest.mark.gpu
+
+WORDS = [1, 2, 4, 8, 16]
+
+
+@pytest.fixture(scope="module")
+def kh():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    import paper_2006_03372_gb300 as kh
+    kh.load_library()
+    return kh
+
+
+def _run(kh, g, h, words=0, rounds=False):
+    with kh.KHCore.from_graph(g, words=words) as ctx:
+        d = ctx.hdegrees(h)
+        c, r, st = ctx.decompose_ex(h)
+    return d, c, r, st
+
+
+def test_fig1_example(kh, fig1):
+    g, vals = fig1
+    for h in [1, 2, 3, 4]:
+        d, c, r, st = _run(kh, g, h)
+        assert (d == oracle.hdegrees(g, h)).all()
+        assert (c == oracle.peel(g, h)).all()
+    d, c, r, st = _run(kh, g, 2)
+    assert (c == np.array([int(x) for x in vals["core_h2"]])).all()
+    # level-synchronous rounds of the example at h=2 (each round one level step)
+    want_r = oracle.level_rounds(g, 2, c)
+    assert st["rounds"] == want_r.max() + 1 and st["k_max"] == 6
+    assert (r == want_r).all()
+
+
+@pytest.mark.parametrize("h", [1, 2, 3, 4, 5])
+def test_small_graphs_all_words(kh, h):
+    for g in small_graphs(40 + h, 9, (2, 300)):
+        want_d = oracle.hdegrees(g, h)
+        want_c = oracle.peel(g, h)
+        for w in WORDS:
+            d, c, r, st = _run(kh, g, h, words=w)
+            assert (d == want_d).all(), (g.name, h, w)
+            assert (c == want_c).all(), (g.name, h, w)
+            fails, _ = oracle.certificate(g, h, c, r)
+            assert fails == 0
+
+
+def test_config1_er_h2_exact(kh):
+    g = gg.config1_er()
+    want = oracle.peel(g, 2)
+    for w in [0, 1, 4, 16]:
+        d, c, r, st = _run(kh, g, 2, words=w)
+        assert (d == oracle.hdegrees(g, 2)).all()
+        assert (c == want).all()
+        assert oracle.certificate(g, 2, c, r)[0] == 0
+
+
+def test_ragged_batches_and_degree_classes(kh):
+    # a hub above the block threshold, medium-degree vertices, a ragged tail
+    parts = [gg.star(2500), gg.chung_lu(3001, 12.0, 2.2, 1500.0, 17), gg.cycle(77), gg.empty(5)]
+    g = gg.disjoint_union(*parts)
+    deg = g.degrees()
+    assert deg.max() > 1024 and ((deg > 32) & (deg <= 1024)).any()
+    for h in [1, 2, 3]:
+        want_d = oracle.hdegrees(g, h)
+        want_c = oracle.peel(g, h)
+        for w in [1, 8, 16]:
+            d, c, r, st = _run(kh, g, h, words=w)
+            assert (d == want_d).all(), (h, w)
+            assert (c == want_c).all(), (h, w)
+
+
+def test_closed_forms(kh):
+    for n in [1, 2, 7, 40]:
+        d, c, _, _ = _run(kh, gg.complete(n), 2)
+        assert (d == n - 1).all() and (c == n - 1).all()
+    for n in [9, 70]:
+        _, c, _, _ = _run(kh, gg.star(n), 2)
+        assert (c == n - 1).all()
+        _, c, _, _ = _run(kh, gg.star(n), 1)
+        assert (c == 1).all()
+    for n in [11, 200]:
+        for h in [1, 2, 3, 5]:
+            d, c, _, _ = _run(kh, gg.cycle(n), h)
+            assert (d == min(2 * h, n - 1)).all()
+            assert (c == (2 * h if 2 * h < n else n - 1)).all()
+            _, c, _, _ = _run(kh, gg.path(n), h)
+            assert (c == min(h, n - 1)).all()
+
+
+def test_edge_cases(kh):
+    # empty graph, single vertex, isolated vertices, h >= n
+    with kh.KHCore(0, np.zeros(1, np.int32), np.zeros(0, np.int32)) as ctx:
+        assert len(ctx.decompose(2)) == 0
+        assert len(ctx.hdegrees(2)) == 0
+    d, c, _, _ = _run(kh, gg.empty(1), 3)
+    assert d[0] == 0 and c[0] == 0
+    d, c, _, _ = _run(kh, gg.empty(100), 2)
+    assert (d == 0).all() and (c == 0).all()
+    g = gg.erdos_renyi_gnm(50, 80, 5)
+    _, c_big, _, _ = _run(kh, g, 10_000)
+    assert (c_big == oracle.peel(g, 49)).all()
+    with kh.KHCore.from_graph(g) as ctx:
+        with pytest.raises(kh.KHCoreError) as ei:
+            ctx.decompose(0)
+        assert ei.value.status == 1
+        with pytest.raises(kh.KHCoreError):
+            ctx.set_words(3)
+
+
+def test_device_pointers_in_and_out(kh):
+    import torch
+    g = gg.chung_lu(4000, 8.0, 2.5, 300.0, 21)
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    col = torch.from_numpy(g.col).cuda()
+    ctx = kh.khcore_create(g.n, rp, col, stream=torch.cuda.current_stream())
+    try:
+        out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        kh.khcore_decompose(ctx, 2, out)
+        assert (out.cpu().numpy() == oracle.peel(g, 2)).all()
+        kh.khcore_hdegrees(ctx, 3, out)
+        assert (out.cpu().numpy() == oracle.hdegrees(g, 3)).all()
+    finally:
+        kh.khcore_destroy(ctx)
+
+
+def test_repeatable_and_order_independent(kh):
+    g = gg.rmat(12, 8, 0.57, 0.19, 0.19, 0.05, 33)
+    perm = np.argsort(gg.Stream(3, "perm").u64(g.n), kind="stable")
+    gp = gg.relabel(g, perm)
+    _, c1, _, _ = _run(kh, g, 3)
+    _, c2, _, _ = _run(kh, g, 3)
+    _, c3, _, _ = _run(kh, gp, 3)
+    assert (c1 == c2).all()
+    assert (c3[perm] == c1).all()
+    assert (c1 == oracle.peel(g, 3)).all()
