@@ -1,0 +1,346 @@
+#!/usr/bin/env python3
+"""Benchmark of the (k,h)-core hot path on GB300.
+
+One step = the whole hot path (initial h-degrees, then level / peel set /
+affected set / recompute rounds until every vertex is peeled) over the
+1e6-vertex Chung-Lu graph (mean degree 20, exponent 2.5, max expected
+degree 1e4, seed 2), once for every h in --hs (default 2 and 3). The CSR is
+resident in HBM before the timed region starts; each step writes the core
+indices to a device buffer.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank decomposes its own replica of the graph on
+its own GPU (the path does not shard); value = all decompositions / slowest
+rank's time. --impl reference times the CPU oracle on a bounded sample of the
+same workload on the host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("(k,h)-core decompose time & h-hop BFS GTEPS (HBM roofline %); "
+          "batched graphs/s, p99")
+UNIT = "decompositions/s"
+WORKLOAD = "chung_lu_n1e6_m1e7_gamma2.5_dmax1e4_seed2"
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse():
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--graph", default="cl1m", help="graphgen.CONFIGS key")
+    p.add_argument("--hs", default="2,3", help="comma-separated h values decomposed per step")
+    p.add_argument("--words", type=int, default=0, help="64-bit source words per vertex (0 = auto)")
+    p.add_argument("--e2e-steps", type=int, default=1)
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU work of the oracle sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# --------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline_sample(g, hs, seconds, rank):
+    """The oracle as it stands on the host cores: plain per-vertex BFS h-degrees
+    (the first step of its peeler) on a bounded vertex sample, extrapolated to
+    the metric's unit. The oracle's decomposition also recomputes h-degrees
+    after every deletion, so the extrapolation is an upper bound on its rate."""
+    import numpy as np
+
+    import graphgen as gg
+    import oracle
+    rng = gg.Stream(99, "cpu-sample")
+    per_h = {}
+    for h in hs:
+        budget = seconds / len(hs)
+        count, spent, sample = 8, 0.0, 0
+        verts_all = np.argsort(rng.u64(g.n), kind="stable").astype(np.int32)
+        pos = 0
+        scanned = 0
+        while spent < budget and pos < g.n:
+            v = verts_all[pos:pos + count]
+            t0 = time.perf_counter()
+            _, sc = oracle.hdegree_list(g, h, v, return_scanned=True)
+            spent += time.perf_counter() - t0
+            scanned += int(sc.sum())
+            sample += len(v)
+            pos += len(v)
+            count = min(count * 2, 4096)
+        per_h[h] = dict(seconds=spent, vertices=sample, scanned=scanned,
+                        est_pass_s=spent * g.n / max(sample, 1))
+    est_step_s = sum(v["est_pass_s"] for v in per_h.values())
+    threads = oracle.threads() or 1
+    return {
+        "value": len(hs) / est_step_s,
+        "unit": UNIT,
+        "cores": threads,
+        "kind": "oracle",
+        "sample": ("oracle plain-BFS h-degrees of " +
+                   ", ".join(f"{v['vertices']} random vertices at h={h} ({v['seconds']:.1f} s)"
+                             for h, v in per_h.items()) +
+                   f", extrapolated to one initial h-degree pass over all {g.n} vertices per h; "
+                   "an upper bound on the oracle's decomposition rate (its per-deletion recomputes "
+                   "are not counted)"),
+        "cpu_gteps": {str(h): v["scanned"] / v["seconds"] / 1e9 for h, v in per_h.items()},
+    }
+
+
+# --------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    import graphgen as gg
+    hs = [int(x) for x in args.hs.split(",")]
+    g = gg.config_graph(args.graph)
+    # each step: a bounded sample, sized so the whole run stays within minutes
+    per_step = max(2.0, min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_baseline_sample(g, hs, per_step / 4, rank)
+    vals = []
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline_sample(g, hs, per_step, rank)
+        vals.append(last["value"])
+    wall = time.perf_counter() - t0
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * len(hs) / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "hs": hs, "n": g.n, "m": g.m},
+        "cpu_baseline": dict(last, value=value),
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import graphgen as gg
+    import paper_2006_03372_gb300 as kh
+
+    world, rank, local = dist_setup(args)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    hs = [int(x) for x in args.hs.split(",")]
+    g = gg.config_graph(args.graph)
+    stream = torch.cuda.current_stream()
+
+    rp_d = torch.from_numpy(g.row_ptr).cuda()
+    col_d = torch.from_numpy(g.col).cuda()
+    ctx = kh.khcore_create(g.n, rp_d, col_d, kh.FLAG_TRUST_INPUT, stream)
+    if args.words:
+        kh.khcore_set_words(ctx, args.words)
+    kh.khcore_set_profiling(ctx, 1)
+    core_d = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def step(collect=None):
+        for h in hs:
+            flush.zero_()  # inputs and state are larger than L2 too; flush anyway
+            c, r, st = kh.khcore_decompose_ex(ctx, h, core_d, want_rounds=False)
+            if collect is not None:
+                collect.append(st)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    stats = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(stats)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+        pg.barrier()
+    ms_per_step = ms / args.steps
+    value = world * args.steps * len(hs) / (ms / 1e3)
+
+    # kernel-level roofline for the dominant kernel (the BFS level kernel)
+    lvl_ms = sum(s["level_ms"] for s in stats)
+    lvl_launch = sum(s["level_launches"] for s in stats)
+    lvl_bytes = sum(s["level_bytes"] for s in stats)
+    edges = sum(s["edges_traversed"] for s in stats)
+    peak, peak_kind = load_peaks()
+    achieved = (lvl_bytes / lvl_launch) / (lvl_ms / lvl_launch / 1e3) / 1e9 if lvl_ms > 0 else None
+
+    # end to end through the public API with host buffers
+    rp_h = torch.from_numpy(g.row_ptr).pin_memory()
+    col_h = torch.from_numpy(g.col).pin_memory()
+    core_h = torch.empty(g.n, dtype=torch.int32).pin_memory()
+    e2e_times = []
+    for _ in range(args.e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c2 = kh.khcore_create(g.n, rp_h, col_h, kh.FLAG_TRUST_INPUT, stream)
+        if args.words:
+            kh.khcore_set_words(c2, args.words)
+        for h in hs:
+            kh.khcore_decompose(c2, h, core_h)
+        kh.khcore_destroy(c2)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = statistics.median(e2e_times)
+    if pg:
+        t = torch.tensor([e2e_s], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    st_last = {h: stats[-len(hs) + i] for i, h in enumerate(hs)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": g.n, "m": g.m, "hs": hs,
+                   "words_per_vertex": stats[-1]["words_per_vertex"],
+                   "l2": "2x-L2 buffer written before every decomposition; working set > L2",
+                   "parallelism": f"replicas{world}"},
+        "decompose_ms": {str(h): st_last[h]["device_ms"] for h in hs},
+        "rounds": {str(h): st_last[h]["rounds"] for h in hs},
+        "gteps": edges / (ms / 1e3) / 1e9,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None, "traffic": None,
+                     "kernel": "k_pull (one multi-source BFS level)",
+                     "peak_kind": peak_kind},
+        "clocks": clk,
+        "e2e": {"value": world * len(hs) / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(4 * (g.n + 1 + g.m_directed)),
+                "d2h_bytes_per_step": int(4 * g.n * len(hs))},
+        "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample(g, hs, args.cpu_seconds, rank)
+    kh.khcore_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -69,6 +69,15 @@ typedef struct {
     int64_t source_batches;    /* multi-source BFS batches run, initial pass included */
     int64_t kernel_launches;   /* kernels launched by this call */
     double device_ms;          /* device time of the call (CUDA events) */
+    int64_t edges_traversed;   /* CSR entries a plain single-source h-bounded BFS
+                                  would scan, summed over every source of every
+                                  h-degree computation of the call */
+    /* Filled only while profiling is on (khcore_set_profiling): */
+    int64_t level_launches;    /* BFS level kernel launches timed */
+    double level_ms;           /* their summed device time (CUDA events) */
+    double level_bytes;        /* their summed algorithmic bytes: per launch
+                                  4*n_b + 4*m_b + 16*W*n_b for the n_b alive
+                                  rows and m_b CSR entries it scans */
 } khcore_stats;
 
 /*
@@ -133,6 +142,23 @@ int64_t khcore_num_entries(const khcore_ctx *ctx);
  * otherwise); 0 restores the automatic choice. Results do not depend on W.
  */
 khcore_status khcore_set_words(khcore_ctx *ctx, int32_t words);
+
+/*
+ * khcore_set_push_alpha — direction choice of the multi-source BFS: a level
+ * expands in the push direction (frontier vertices scatter to neighbours)
+ * when (sum of frontier degrees) * alpha < CSR entries of the alive graph,
+ * and in the pull direction (every alive vertex gathers) otherwise. Default
+ * 16; 0 forces pull everywhere. alpha < 0 is EINVAL. Results do not depend
+ * on alpha.
+ */
+khcore_status khcore_set_push_alpha(khcore_ctx *ctx, int32_t alpha);
+
+/*
+ * khcore_set_profiling — when on (nonzero), every BFS level kernel launch is
+ * bracketed by CUDA events on the context's stream and khcore_stats reports
+ * their count, summed time and algorithmic bytes. Results do not change.
+ */
+khcore_status khcore_set_profiling(khcore_ctx *ctx, int32_t on);
 
 /* Release every device and host resource of the context. NULL is a no-op. */
 void khcore_destroy(khcore_ctx *ctx);

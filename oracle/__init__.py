@@ -53,7 +53,7 @@ def _load():
         i32, i64 = ctypes.c_int32, ctypes.c_int64
         lib.orc_hdegrees.argtypes = [i32, P, P, P, i32, P]
         lib.orc_hdegrees.restype = ctypes.c_int
-        lib.orc_hdegree_list.argtypes = [i32, P, P, P, i32, i64, P, P]
+        lib.orc_hdegree_list.argtypes = [i32, P, P, P, i32, i64, P, P, P]
         lib.orc_hdegree_list.restype = ctypes.c_int
         lib.orc_peel.argtypes = [i32, P, P, i32, P, P]
         lib.orc_peel.restype = ctypes.c_int
@@ -104,14 +104,19 @@ def hdegrees(g, h: int, alive=None) -> np.ndarray:
     return out[: g.n]
 
 
-def hdegree_list(g, h: int, verts, alive=None) -> np.ndarray:
+def hdegree_list(g, h: int, verts, alive=None, return_scanned: bool = False):
+    """d_v^h for the listed vertices; with return_scanned also the number of
+    CSR entries each BFS scanned (sum of deg(x) over x at distance < h)."""
     lib = _load()
     rp, col = _csr(g)
     v = np.ascontiguousarray(verts, dtype=np.int32)
     out = np.zeros(max(len(v), 1), dtype=np.int32)
+    sc = np.zeros(max(len(v), 1), dtype=np.int64)
     al = _alive(alive, g.n)
-    if lib.orc_hdegree_list(g.n, _p(rp), _p(col), _p(al), int(h), len(v), _p(v), _p(out)) != 0:
+    if lib.orc_hdegree_list(g.n, _p(rp), _p(col), _p(al), int(h), len(v), _p(v), _p(out), _p(sc)) != 0:
         raise MemoryError("oracle: out of memory")
+    if return_scanned:
+        return out[: len(v)], sc[: len(v)]
     return out[: len(v)]
 
 

@@ -49,10 +49,10 @@
 /* If ball != NULL the visited vertices other than v are appended to it.     */
 /* Returns |{u != v : dist(v,u) <= h}|.                                      */
 /* ------------------------------------------------------------------------ */
-static int64_t bfs_count(int32_t v, int32_t h, const int32_t *row_ptr,
-                         const int32_t *col, const uint8_t *alive,
-                         int32_t *dist, int32_t *queue, int32_t *ball,
-                         int64_t *ball_len)
+static int64_t bfs_count_scan(int32_t v, int32_t h, const int32_t *row_ptr,
+                              const int32_t *col, const uint8_t *alive,
+                              int32_t *dist, int32_t *queue, int32_t *ball,
+                              int64_t *ball_len, int64_t *scanned)
 {
     int64_t head = 0, tail = 0;
     queue[tail++] = v;
@@ -60,6 +60,7 @@ static int64_t bfs_count(int32_t v, int32_t h, const int32_t *row_ptr,
     while (head < tail) {
         int32_t x = queue[head++];
         if (dist[x] == h) continue;           /* do not expand past radius h */
+        if (scanned) *scanned += row_ptr[x + 1] - row_ptr[x];
         for (int32_t e = row_ptr[x]; e < row_ptr[x + 1]; e++) {
             int32_t y = col[e];
             if (alive && !alive[y]) continue; /* paths stay inside G[alive] */
@@ -74,6 +75,14 @@ static int64_t bfs_count(int32_t v, int32_t h, const int32_t *row_ptr,
         dist[x] = -1;
     }
     return tail - 1;
+}
+
+static int64_t bfs_count(int32_t v, int32_t h, const int32_t *row_ptr,
+                         const int32_t *col, const uint8_t *alive,
+                         int32_t *dist, int32_t *queue, int32_t *ball,
+                         int64_t *ball_len)
+{
+    return bfs_count_scan(v, h, row_ptr, col, alive, dist, queue, ball, ball_len, NULL);
 }
 
 /* d_v^h(G[alive]) for every vertex; -1 for vertices that are not alive.
@@ -103,10 +112,12 @@ int orc_hdegrees(int32_t n, const int32_t *row_ptr, const int32_t *col,
     return ok;
 }
 
-/* h-hop degree of a list of vertices (used for spot checks on large graphs). */
+/* h-hop degree of a list of vertices (used for spot checks on large graphs).
+ * scanned_out (nullable, one per listed vertex) receives the number of CSR
+ * entries the BFS scanned, i.e. the sum of deg(x) over x with dist < h. */
 int orc_hdegree_list(int32_t n, const int32_t *row_ptr, const int32_t *col,
                      const uint8_t *alive, int32_t h, int64_t count,
-                     const int32_t *verts, int32_t *deg_out)
+                     const int32_t *verts, int32_t *deg_out, int64_t *scanned_out)
 {
     int ok = 0;
 #pragma omp parallel
@@ -121,8 +132,10 @@ int orc_hdegree_list(int32_t n, const int32_t *row_ptr, const int32_t *col,
 #pragma omp for schedule(dynamic, 1)
             for (int64_t i = 0; i < count; i++) {
                 int32_t v = verts[i];
+                int64_t sc = 0;
                 deg_out[i] = (alive && !alive[v]) ? -1
-                    : (int32_t)bfs_count(v, h, row_ptr, col, alive, dist, queue, NULL, NULL);
+                    : (int32_t)bfs_count_scan(v, h, row_ptr, col, alive, dist, queue, NULL, NULL, &sc);
+                if (scanned_out) scanned_out[i] = sc;
             }
         }
         free(dist);

@@ -27,7 +27,9 @@ from ._build import build as _build_lib
 
 __all__ = [
     "KHCoreError", "khcore_create", "khcore_hdegrees", "khcore_decompose", "khcore_decompose_ex",
-    "khcore_destroy", "khcore_last_error", "khcore_set_words", "khcore_status_string", "Stats",
+    "khcore_destroy", "khcore_last_error", "khcore_set_words", "khcore_set_profiling",
+    "khcore_set_push_alpha",
+    "khcore_status_string", "Stats",
     "KHCore", "library_path", "load_library",
 ]
 
@@ -46,7 +48,9 @@ class Stats(ctypes.Structure):
     _fields_ = [("h", ctypes.c_int32), ("rounds", ctypes.c_int32), ("k_max", ctypes.c_int32),
                 ("words_per_vertex", ctypes.c_int32), ("deleted_total", ctypes.c_int64),
                 ("affected_total", ctypes.c_int64), ("source_batches", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64), ("device_ms", ctypes.c_double)]
+                ("kernel_launches", ctypes.c_int64), ("device_ms", ctypes.c_double),
+                ("edges_traversed", ctypes.c_int64), ("level_launches", ctypes.c_int64),
+                ("level_ms", ctypes.c_double), ("level_bytes", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -90,6 +94,10 @@ def load_library(build_if_missing: bool = False):
         lib.khcore_status_string.restype = ctypes.c_char_p
         lib.khcore_set_words.argtypes = [P, i32]
         lib.khcore_set_words.restype = ctypes.c_int
+        lib.khcore_set_push_alpha.argtypes = [P, i32]
+        lib.khcore_set_push_alpha.restype = ctypes.c_int
+        lib.khcore_set_profiling.argtypes = [P, i32]
+        lib.khcore_set_profiling.restype = ctypes.c_int
         lib.khcore_num_vertices.argtypes = [P]
         lib.khcore_num_vertices.restype = i32
         lib.khcore_num_entries.argtypes = [P]
@@ -165,6 +173,16 @@ def khcore_set_words(ctx, words: int) -> None:
     _check(lib, ctx, lib.khcore_set_words(ctx, int(words)))
 
 
+def khcore_set_push_alpha(ctx, alpha: int) -> None:
+    lib = load_library()
+    _check(lib, ctx, lib.khcore_set_push_alpha(ctx, int(alpha)))
+
+
+def khcore_set_profiling(ctx, on: int) -> None:
+    lib = load_library()
+    _check(lib, ctx, lib.khcore_set_profiling(ctx, int(on)))
+
+
 def _out(ctx, out):
     n = load_library().khcore_num_vertices(ctx)
     if out is None:
@@ -209,11 +227,13 @@ def khcore_decompose_ex(ctx, h: int, core_out=None, round_out=None, want_rounds:
 class KHCore:
     """Context manager around one device-resident graph."""
 
-    def __init__(self, n, row_ptr, col, flags: int = 0, stream=None, words: int = 0):
+    def __init__(self, n, row_ptr, col, flags: int = 0, stream=None, words: int = 0, alpha=None):
         self.ctx = khcore_create(n, row_ptr, col, flags, stream)
         self.n = int(n)
         if words:
             khcore_set_words(self.ctx, words)
+        if alpha is not None:
+            khcore_set_push_alpha(self.ctx, alpha)
 
     @classmethod
     def from_graph(cls, g, **kw):

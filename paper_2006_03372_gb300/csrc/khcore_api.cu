@@ -42,9 +42,22 @@ struct khcore_ctx {
     int W_alloc = 0;
     uint64_t *V = nullptr, *F[2] = {nullptr, nullptr};
     uint8_t *flag[2] = {nullptr, nullptr};
+    int32_t *Q[3] = {nullptr, nullptr, nullptr};
+    int32_t *QH[3] = {nullptr, nullptr, nullptr};
+    int32_t *T = nullptr;
+    LevelCtl *ctl = nullptr;
     int32_t *cnt = nullptr;
+    int32_t push_alpha = 16;  // push when frontier degree sum * alpha < alive CSR entries
+    unsigned long long *edges = nullptr;  // device counter of plain-BFS-equivalent edges
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+    // profiling: an event pair around every BFS level launch
+    bool profiling = false;
+    std::vector<cudaEvent_t> tev;
+    LevelTimer timer{nullptr, 0, 0};
+    double level_ms = 0.0;
+    int64_t level_launches = 0;
 
     GraphView view() const
     {
@@ -207,6 +220,8 @@ khcore_status ensure_bfs(khcore_ctx *c, int W)
     CU(dev_alloc(&c->F[1], words));
     CU(dev_alloc(&c->cnt, (size_t)64 * W));
     CU(cudaMemsetAsync(c->V, 0, words * sizeof(uint64_t), c->stream));
+    CU(cudaMemsetAsync(c->F[0], 0, words * sizeof(uint64_t), c->stream));
+    CU(cudaMemsetAsync(c->F[1], 0, words * sizeof(uint64_t), c->stream));
     CU(cudaMemsetAsync(c->cnt, 0, (size_t)64 * W * sizeof(int32_t), c->stream));
     c->W_alloc = W;
     return KHCORE_OK;
@@ -214,9 +229,25 @@ khcore_status ensure_bfs(khcore_ctx *c, int W)
 
 int bfs_grid(khcore_ctx *c, int W) { return c->sm_count * max_blocks_per_sm_bfs(W); }
 
+// Sum the timed level launches recorded so far (waits for the last one).
+khcore_status flush_timer(khcore_ctx *c)
+{
+    if (!c->profiling || c->timer.used == 0) return KHCORE_OK;
+    CU(cudaEventSynchronize(c->timer.ev[2 * c->timer.used - 1]));
+    for (int i = 0; i < c->timer.used; i++) {
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, c->timer.ev[2 * i], c->timer.ev[2 * i + 1]));
+        c->level_ms += ms;
+    }
+    c->level_launches += c->timer.used;
+    c->timer.used = 0;
+    return KHCORE_OK;
+}
+
 // h-degrees of the sources src[0..ns) in G[alive], in batches of 64*W.
-khcore_status hdeg_sources(khcore_ctx *c, int W, int32_t h, int32_t ns, int64_t *batches,
-                           int64_t *launches)
+// n_b / m_b: alive rows and their CSR entries (for the algorithmic bytes).
+khcore_status hdeg_sources(khcore_ctx *c, int W, int32_t h, int32_t ns, int64_t n_b, int64_t m_b,
+                           khcore_stats *stt)
 {
     const GraphView g = c->view();
     BfsBufs b;
@@ -225,13 +256,31 @@ khcore_status hdeg_sources(khcore_ctx *c, int W, int32_t h, int32_t ns, int64_t 
     b.F[1] = c->F[1];
     b.flag[0] = c->flag[0];
     b.flag[1] = c->flag[1];
+    for (int k = 0; k < 3; k++) {
+        b.Q[k] = c->Q[k];
+        b.QH[k] = c->QH[k];
+    }
+    b.T = c->T;
+    b.ctl = c->ctl;
     b.cnt = c->cnt;
+    b.edges = c->edges;
+    BfsTuning tune;
+    tune.alpha = c->push_alpha;
+    tune.m_alive = (unsigned long long)m_b;
     const int32_t S = 64 * W;
     const int grid = bfs_grid(c, W);
     for (int32_t off = 0; off < ns; off += S) {
         const int32_t cur = std::min(S, ns - off);
-        CU(run_bfs_batch(W, g, c->alive, b, c->src + off, cur, h, c->deg, grid, c->stream, launches));
-        if (batches) ++*batches;
+        if (c->profiling && c->timer.used + h > c->timer.cap) {
+            khcore_status s = flush_timer(c);
+            if (s != KHCORE_OK) return s;
+        }
+        CU(run_bfs_batch(W, g, c->alive, b, c->src + off, cur, h, c->deg, tune, grid, c->stream,
+                         stt ? &stt->kernel_launches : nullptr, c->profiling ? &c->timer : nullptr));
+        if (stt) {
+            stt->source_batches++;
+            if (c->profiling) stt->level_bytes += (double)h * (4.0 * n_b + 4.0 * m_b + 16.0 * W * n_b);
+        }
     }
     return KHCORE_OK;
 }
@@ -301,7 +350,15 @@ void khcore_destroy(khcore_ctx *c)
     cudaFree(c->F[1]);
     cudaFree(c->flag[0]);
     cudaFree(c->flag[1]);
+    for (int k = 0; k < 3; k++) {
+        cudaFree(c->Q[k]);
+        cudaFree(c->QH[k]);
+    }
+    cudaFree(c->T);
+    cudaFree(c->ctl);
     cudaFree(c->cnt);
+    cudaFree(c->edges);
+    for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
     if (c->st_host) cudaFreeHost(c->st_host);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
@@ -390,8 +447,16 @@ khcore_status khcore_create(int32_t n, const int32_t *row_ptr, const int32_t *co
         A(dev_alloc(&c->aff[1], nw));
         A(dev_alloc(&c->vis, nw));
         A(dev_alloc(&c->st, 1));
-        A(dev_alloc(&c->flag[0], (size_t)n));
-        A(dev_alloc(&c->flag[1], (size_t)n));
+        A(dev_alloc(&c->edges, 1));
+        const size_t nflag = (((size_t)n + 3) / 4) * 4;  // whole 32-bit words (flag claims)
+        A(dev_alloc(&c->flag[0], nflag));
+        A(dev_alloc(&c->flag[1], nflag));
+        for (int k = 0; k < 3; k++) {
+            A(dev_alloc(&c->Q[k], (size_t)n));
+            A(dev_alloc(&c->QH[k], (size_t)n));
+        }
+        A(dev_alloc(&c->T, (size_t)n));
+        A(dev_alloc(&c->ctl, 1));
         if (st != KHCORE_OK) break;
         e = cudaMallocHost((void **)&c->st_host, sizeof(PeelState));
         if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
@@ -404,6 +469,8 @@ khcore_status khcore_create(int32_t n, const int32_t *row_ptr, const int32_t *co
         if (e == cudaSuccess && n)
             e = cudaMemcpyAsync(c->classes, classes.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice,
                                 c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->flag[0], 0, nflag, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->flag[1], 0, nflag, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) {
             st = fail(nullptr, KHCORE_ECUDA, "graph upload: %s", cudaGetErrorString(e));
@@ -427,6 +494,32 @@ khcore_status khcore_set_words(khcore_ctx *c, int32_t words)
     return KHCORE_OK;
 }
 
+khcore_status khcore_set_push_alpha(khcore_ctx *c, int32_t alpha)
+{
+    if (!c) return KHCORE_EINVAL;
+    if (alpha < 0) return fail(c, KHCORE_EINVAL, "alpha must be >= 0 (got %d)", alpha);
+    c->push_alpha = alpha;
+    return KHCORE_OK;
+}
+
+khcore_status khcore_set_profiling(khcore_ctx *c, int32_t on)
+{
+    if (!c) return KHCORE_EINVAL;
+    if (on && c->tev.empty()) {
+        const int cap = 1024;  // event pairs between two summations
+        c->tev.resize(2 * cap, nullptr);
+        for (auto &e : c->tev) {
+            cudaError_t err = cudaEventCreate(&e);
+            if (err != cudaSuccess) return fail(c, KHCORE_ECUDA, "cudaEventCreate: %s", cudaGetErrorString(err));
+        }
+        c->timer.ev = c->tev.data();
+        c->timer.cap = cap;
+    }
+    c->profiling = on != 0;
+    c->timer.used = 0;
+    return KHCORE_OK;
+}
+
 khcore_status khcore_hdegrees(khcore_ctx *c, int32_t h, int32_t *deg_out)
 {
     khcore_status s = check_ctx(c);
@@ -439,7 +532,7 @@ khcore_status khcore_hdegrees(khcore_ctx *c, int32_t h, int32_t *deg_out)
     const int32_t he = effective_h(c->n, h);
     CU(launch_alive_init(c->alive, c->n, c->stream));
     CU(launch_iota(c->src, c->n, c->stream));
-    if ((s = hdeg_sources(c, W, he, c->n, nullptr, nullptr)) != KHCORE_OK) return s;
+    if ((s = hdeg_sources(c, W, he, c->n, c->n, c->m, nullptr)) != KHCORE_OK) return s;
     if ((s = write_out(c, deg_out, c->deg)) != KHCORE_OK) return s;
     CU(cudaStreamSynchronize(c->stream));
     return KHCORE_OK;
@@ -473,12 +566,17 @@ khcore_status khcore_decompose_ex(khcore_ctx *c, int32_t h, int32_t *core_out, i
     std::memset(&init, 0, sizeof init);
     init.min_deg = INT_MAX;
     init.alive = c->n;
+    init.m_alive = (unsigned long long)c->m;
     *c->st_host = init;
+    c->level_ms = 0.0;
+    c->level_launches = 0;
+    c->timer.used = 0;
     CU(cudaMemcpyAsync(c->st, c->st_host, sizeof(PeelState), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemsetAsync(c->edges, 0, sizeof(unsigned long long), c->stream));
     CU(launch_alive_init(c->alive, c->n, c->stream));
     CU(launch_iota(c->src, c->n, c->stream));
     stt.kernel_launches += 2;
-    if ((s = hdeg_sources(c, W, he, c->n, &stt.source_batches, &stt.kernel_launches)) != KHCORE_OK) return s;
+    if ((s = hdeg_sources(c, W, he, c->n, c->n, c->m, &stt)) != KHCORE_OK) return s;
 
     int32_t round = 0;
     for (;;) {
@@ -506,8 +604,7 @@ khcore_status khcore_decompose_ex(khcore_ctx *c, int32_t h, int32_t *core_out, i
         stt.k_max = ps.k;
         round++;
         if (ps.alive == 0) break;
-        if (ps.nA > 0 &&
-            (s = hdeg_sources(c, W, he, ps.nA, &stt.source_batches, &stt.kernel_launches)) != KHCORE_OK)
+        if (ps.nA > 0 && (s = hdeg_sources(c, W, he, ps.nA, ps.alive, (int64_t)ps.m_alive, &stt)) != KHCORE_OK)
             return s;
         // advance the device-side round counter
         c->st_host->round = round;
@@ -517,10 +614,17 @@ khcore_status khcore_decompose_ex(khcore_ctx *c, int32_t h, int32_t *core_out, i
     CU(cudaEventRecord(c->ev1, c->stream));
     if ((s = write_out(c, core_out, c->core)) != KHCORE_OK) return s;
     if ((s = write_out(c, round_out, c->rnd)) != KHCORE_OK) return s;
+    unsigned long long edges = 0;
+    CU(cudaMemcpyAsync(&edges, c->edges, sizeof edges, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     float ms = 0.f;
     CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
     stt.device_ms = ms;
+    stt.edges_traversed = (int64_t)edges;
+    if ((s = flush_timer(c)) != KHCORE_OK) return s;
+    stt.level_ms = c->level_ms;
+    stt.level_launches = c->level_launches;
+    if (!c->profiling) stt.level_bytes = 0;
     if (stats) *stats = stt;
     return KHCORE_OK;
 }

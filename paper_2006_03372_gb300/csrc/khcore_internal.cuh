@@ -27,21 +27,59 @@ struct GraphView {
     int32_t n_light, n_medium, n_heavy;
 };
 
+// Frontier bookkeeping of one BFS batch, device-resident. Levels use a ring
+// of three slots: level l reads slot l%3, appends the next frontier to slot
+// (l+1)%3, and slot (l+2)%3 is reset by the level's post kernel.
+struct LevelCtl {
+    int32_t q[3];                // |Q| per slot: frontier vertex lists
+    int32_t qh[3];               // |QH| per slot: frontier vertices with deg > kPushChunk
+    unsigned long long fe[3];    // sum of CSR degrees over Q (direction choice)
+    int32_t t;                   // |T|: vertices whose V row is nonzero
+    int32_t pad;
+};
+
+// A frontier vertex with more CSR entries than this is expanded by every
+// warp of the grid in the push direction (hub splitting).
+constexpr int kPushChunk = 256;
+
 // Multi-source BFS state for one batch of 64*W sources. Vertex-major: the W
 // words of vertex y are V[y*W .. y*W+W-1]; bit b of word j is source 64*j+b
 // of the batch.
-//   V        visited (sources within distance < current level); all zero
-//            between batches
-//   F[2]     frontier words of the current / next level; only meaningful
-//            where the matching flag byte is 1
+//   V        visited (distance < current level); rows zero between batches
+//            except those listed in T
+//   F[2]     frontier words of the current / next level; a row is nonzero
+//            only while its vertex is in that level's list Q
 //   flag[2]  one byte per vertex: 1 iff the vertex is in that frontier
+//   Q[3], QH[3], T  frontier lists (ring of three) and touched-row list
+//   ctl      list lengths and frontier degree sums
 //   cnt      [64*W] per-source count of newly reached vertices; zero between
 //            batches
+//   edges    plain-BFS-equivalent CSR entries scanned: sum over sources s and
+//            vertices x with dist(s, x) < h of deg(x) (for GTEPS reporting)
 struct BfsBufs {
     uint64_t *V;
     uint64_t *F[2];
     uint8_t *flag[2];
+    int32_t *Q[3];
+    int32_t *QH[3];
+    int32_t *T;
+    LevelCtl *ctl;
     int32_t *cnt;
+    unsigned long long *edges;
+};
+
+// Direction choice of one level: push when (sum of frontier degrees) * alpha
+// < CSR entries of the alive graph, else pull.
+struct BfsTuning {
+    int32_t alpha;
+    unsigned long long m_alive;
+};
+
+// Optional CUDA-event timing of every BFS level launch.
+struct LevelTimer {
+    cudaEvent_t *ev;   // pool of 2*cap events
+    int cap;
+    int used;          // pairs recorded so far
 };
 
 // Round state of the peeler, device-resident.
@@ -54,6 +92,7 @@ struct PeelState {
     int32_t round;    // current round
     int32_t err;      // device-side consistency error code (0 = none)
     int32_t pad;
+    unsigned long long m_alive;  // CSR entries of alive vertices
 };
 
 // ---- launchers (khcore_kernels.cu) -----------------------------------------
@@ -64,15 +103,18 @@ cudaError_t launch_alive_init(uint32_t *alive, int32_t n, cudaStream_t s);
 
 // One MS-BFS batch: sources src[0..ns) (ns <= 64*W), alive mask, h levels;
 // on return deg[src[i]] = |{u != src[i] alive : dist <= h}| in G[alive].
-// grid = number of blocks for the expansion kernels.
+// grid = number of blocks for the level kernels.
+// timer (nullable): an event pair is recorded around each level launch
+// while pairs are left in the pool.
 cudaError_t run_bfs_batch(int W, const GraphView &g, const uint32_t *alive, const BfsBufs &b,
-                          const int32_t *src, int32_t ns, int32_t h, int32_t *deg,
-                          int grid, cudaStream_t s, int64_t *launches);
+                          const int32_t *src, int32_t ns, int32_t h, int32_t *deg, BfsTuning tune,
+                          int grid, cudaStream_t s, int64_t *launches, LevelTimer *timer);
 
 // Peel round pieces.
 cudaError_t launch_min_alive_deg(const GraphView &g, const uint32_t *alive, const int32_t *deg,
                                  PeelState *st, int grid, cudaStream_t s);
 cudaError_t launch_set_level(PeelState *st, cudaStream_t s);
+// Also subtracts the CSR degree of every deleted vertex from st->m_alive.
 cudaError_t launch_peel_compact(const GraphView &g, uint32_t *alive, const int32_t *deg,
                                 PeelState *st, int32_t *core, int32_t *rnd, uint32_t *fr0,
                                 int grid, cudaStream_t s);

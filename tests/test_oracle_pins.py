@@ -252,3 +252,14 @@ def test_certificate_rejects_uniform_shift():
     r = oracle.level_rounds(g, 2, c)
     assert oracle.certificate(g, 2, c + 1, r)[0] > 0
     assert oracle.certificate(g, 2, np.maximum(c - 1, 0), r)[0] > 0
+
+
+def test_hdegree_list_scanned_edges_closed_form():
+    # a BFS to radius h scans the rows of every vertex at distance < h
+    g = gg.path(10)
+    d, sc = oracle.hdegree_list(g, 2, [0, 5], return_scanned=True)
+    assert list(d) == [2, 4]
+    assert list(sc) == [1 + 2, 2 + 2 + 2]
+    s = gg.star(8)
+    d, sc = oracle.hdegree_list(s, 2, [0, 3], return_scanned=True)
+    assert list(d) == [7, 7] and list(sc) == [7 + 7 * 1, 1 + 7]
