@@ -4,6 +4,7 @@
 #include <climits>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -578,6 +579,9 @@ khcore_status khcore_decompose_ex(khcore_ctx *c, int32_t h, int32_t *core_out, i
     stt.kernel_launches += 2;
     if ((s = hdeg_sources(c, W, he, c->n, c->n, c->m, &stt)) != KHCORE_OK) return s;
 
+    // KHCORE_TRACE=1 prints one line per peel round to stderr (tracing aid)
+    const char *trace_env = getenv("KHCORE_TRACE");
+    const bool trace = trace_env && trace_env[0] == '1';
     int32_t round = 0;
     for (;;) {
         // one round: level, peel set D, affected set A, recompute deg[A]
@@ -601,6 +605,14 @@ khcore_status khcore_decompose_ex(khcore_ctx *c, int32_t h, int32_t *core_out, i
             return fail(c, KHCORE_EINTERNAL, "round %d deleted no vertex with %d alive", round, ps.alive);
         stt.deleted_total += ps.nD;
         stt.affected_total += ps.nA;
+        if (trace) {
+            float tms = 0.f;
+            cudaEventRecord(c->ev1, c->stream);
+            cudaEventSynchronize(c->ev1);
+            cudaEventElapsedTime(&tms, c->ev0, c->ev1);
+            fprintf(stderr, "khcore round %d: k=%d |D|=%d |A|=%d alive=%d m_alive=%llu t=%.1f ms\n", round,
+                    ps.k, ps.nD, ps.nA, ps.alive, (unsigned long long)ps.m_alive, tms);
+        }
         stt.k_max = ps.k;
         round++;
         if (ps.alive == 0) break;

@@ -141,7 +141,8 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
 
 __device__ __forceinline__ bool use_push(const LevelCtl *ctl, int slot, BfsTuning tune)
 {
-    return (unsigned long long)ctl->fe[slot] * (unsigned long long)tune.alpha < tune.m_alive;
+    return tune.alpha > 0 &&
+           (unsigned long long)ctl->fe[slot] * (unsigned long long)tune.alpha < tune.m_alive;
 }
 
 // Append y (already claimed in the next frontier) to Q, and to QH if heavy.

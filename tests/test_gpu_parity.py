@@ -49,11 +49,15 @@ def test_small_graphs_all_words(kh, h):
         want_d = oracle.hdegrees(g, h)
         want_c = oracle.peel(g, h)
         for w in WORDS:
-            d, c, r, st = _run(kh, g, h, words=w)
-            assert (d == want_d).all(), (g.name, h, w)
-            assert (c == want_c).all(), (g.name, h, w)
-            fails, _ = oracle.certificate(g, h, c, r)
-            assert fails == 0
+            for alpha in [0, 16, 1 << 20]:
+                with kh.KHCore.from_graph(g, words=w, alpha=alpha) as ctx:
+                    d = ctx.hdegrees(h)
+                    c, r, st = ctx.decompose_ex(h)
+                assert (d == want_d).all(), (g.name, h, w, alpha)
+                assert (c == want_c).all(), (g.name, h, w, alpha)
+                if alpha == 16:
+                    fails, _ = oracle.certificate(g, h, c, r)
+                    assert fails == 0
 
 
 def test_config1_er_h2_exact(kh):
@@ -68,17 +72,19 @@ def test_config1_er_h2_exact(kh):
 
 def test_ragged_batches_and_degree_classes(kh):
     # a hub above the block threshold, medium-degree vertices, a ragged tail
-    parts = [gg.star(2500), gg.chung_lu(3001, 12.0, 2.2, 1500.0, 17), gg.cycle(77), gg.empty(5)]
+    parts = [gg.star(1100), gg.chung_lu(1501, 6.0, 2.2, 700.0, 17), gg.cycle(77), gg.empty(5)]
     g = gg.disjoint_union(*parts)
     deg = g.degrees()
     assert deg.max() > 1024 and ((deg > 32) & (deg <= 1024)).any()
     for h in [1, 2, 3]:
         want_d = oracle.hdegrees(g, h)
-        want_c = oracle.peel(g, h)
+        want_c = oracle.peel(g, h) if h < 3 else None
         for w in [1, 8, 16]:
-            d, c, r, st = _run(kh, g, h, words=w)
-            assert (d == want_d).all(), (h, w)
-            assert (c == want_c).all(), (h, w)
+            for alpha in [0, 16, 1 << 20]:  # pull only, automatic, push wherever possible
+                with kh.KHCore.from_graph(g, words=w, alpha=alpha) as ctx:
+                    assert (ctx.hdegrees(h) == want_d).all(), (h, w, alpha)
+                    if want_c is not None:
+                        assert (ctx.decompose(h) == want_c).all(), (h, w, alpha)
 
 
 def test_closed_forms(kh):
