@@ -132,9 +132,40 @@ khcore_status khcore_decompose(khcore_ctx *ctx, int32_t h, int32_t *core_out);
 khcore_status khcore_decompose_ex(khcore_ctx *ctx, int32_t h, int32_t *core_out,
                                   int32_t *round_out, khcore_stats *stats);
 
-/* Number of vertices and directed CSR entries of the context's graph. */
+/*
+ * khcore_batch_create — one context holding G independent graphs (batching
+ * many graphs of uneven size into the same kernel launches). The graphs are
+ * packed: graph g has n_g = v_off[g+1] - v_off[g] vertices and
+ * m_g = e_off[g+1] - e_off[g] CSR entries;
+ *   v_off, e_off     int64[G+1], v_off[0] = e_off[0] = 0, non-decreasing
+ *   row_ptr_local    int32[v_off[G] + G]: graph g's own row_ptr (n_g + 1
+ *                    entries, starting at 0) at offset v_off[g] + g
+ *   col_local        int32[e_off[G]]: graph g's neighbour ids, local to the
+ *                    graph (0 <= id < n_g), at offset e_off[g]
+ * Each graph must be a valid undirected CSR (as for khcore_create; EINVAL
+ * names the graph otherwise). Vertex v of graph g is vertex v_off[g] + v of
+ * the context: outputs of khcore_hdegrees / khcore_decompose /
+ * khcore_batch_decompose are int32[v_off[G]] in that order. The batch must
+ * fit int32 ids (v_off[G], e_off[G] <= INT32_MAX).
+ */
+khcore_status khcore_batch_create(int32_t G, const int64_t *v_off, const int64_t *e_off,
+                                  const int32_t *row_ptr_local, const int32_t *col_local,
+                                  uint32_t flags, void *stream, khcore_ctx **out);
+
+/*
+ * khcore_batch_decompose — core_h(v) of every vertex of every graph of a
+ * batch context, graph g with its own hop bound h[g] >= 1 (int32[G], host or
+ * device). The graphs peel side by side, each with its own level k (a graph's
+ * core indices are those it would get alone). round_out and stats as for
+ * khcore_decompose_ex; stats->h is the largest h used.
+ */
+khcore_status khcore_batch_decompose(khcore_ctx *ctx, const int32_t *h, int32_t *core_out,
+                                     int32_t *round_out, khcore_stats *stats);
+
+/* Number of vertices, directed CSR entries and graphs of the context. */
 int32_t khcore_num_vertices(const khcore_ctx *ctx);
 int64_t khcore_num_entries(const khcore_ctx *ctx);
+int32_t khcore_num_graphs(const khcore_ctx *ctx);
 
 /*
  * khcore_set_words — choose W, the number of 64-bit source words per vertex

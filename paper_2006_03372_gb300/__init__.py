@@ -30,7 +30,7 @@ __all__ = [
     "khcore_destroy", "khcore_last_error", "khcore_set_words", "khcore_set_profiling",
     "khcore_set_push_alpha",
     "khcore_status_string", "Stats",
-    "KHCore", "library_path", "load_library",
+    "KHCore", "library_path", "load_library", "khcore_batch_create", "khcore_batch_decompose", "pack_graphs",
 ]
 
 STATUS = {0: "KHCORE_OK", 1: "KHCORE_EINVAL", 2: "KHCORE_ENOMEM", 3: "KHCORE_ECUDA",
@@ -102,6 +102,12 @@ def load_library(build_if_missing: bool = False):
         lib.khcore_num_vertices.restype = i32
         lib.khcore_num_entries.argtypes = [P]
         lib.khcore_num_entries.restype = i64
+        lib.khcore_num_graphs.argtypes = [P]
+        lib.khcore_num_graphs.restype = i32
+        lib.khcore_batch_create.argtypes = [i32, P, P, P, P, u32, P, ctypes.POINTER(P)]
+        lib.khcore_batch_create.restype = ctypes.c_int
+        lib.khcore_batch_decompose.argtypes = [P, P, P, P, ctypes.POINTER(Stats)]
+        lib.khcore_batch_decompose.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -222,6 +228,50 @@ def khcore_decompose_ex(ctx, h: int, core_out=None, round_out=None, want_rounds:
     stats = Stats()
     _check(lib, ctx, lib.khcore_decompose_ex(ctx, int(h), pc, pr, ctypes.byref(stats)))
     return core, rnd, stats.as_dict()
+
+
+def khcore_batch_create(v_off, e_off, row_ptr_local, col_local, flags: int = 0, stream=None):
+    """One context over G packed graphs (see include/khcore.h)."""
+    lib = load_library()
+    vo = np.ascontiguousarray(v_off, dtype=np.int64)
+    eo = np.ascontiguousarray(e_off, dtype=np.int64)
+    G = len(vo) - 1
+    rp, k1 = _ptr(row_ptr_local)
+    cl, k2 = _ptr(col_local)
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    out = ctypes.c_void_p()
+    st = lib.khcore_batch_create(G, vo.ctypes.data_as(ctypes.c_void_p), eo.ctypes.data_as(ctypes.c_void_p), rp, cl,
+                                 int(flags), ctypes.c_void_p(stream) if stream else None, ctypes.byref(out))
+    _check(lib, None, st)
+    del k1, k2
+    return _Ctx(out.value)
+
+
+def khcore_batch_decompose(ctx, h, core_out=None, round_out=None, want_rounds: bool = True):
+    """(core, round, stats) of a batch context; h[g] is graph g's hop bound."""
+    lib = load_library()
+    hv, k = _ptr(h)
+    core = _out(ctx, core_out)
+    rnd = _out(ctx, round_out) if (want_rounds or round_out is not None) else None
+    pc, _ = _ptr(core)
+    pr, _ = _ptr(rnd)
+    stats = Stats()
+    _check(lib, ctx, lib.khcore_batch_decompose(ctx, hv, pc, pr, ctypes.byref(stats)))
+    del k
+    return core, rnd, stats.as_dict()
+
+
+def pack_graphs(graphs):
+    """(v_off, e_off, row_ptr_local, col_local) for a list of graphs with
+    .n, .row_ptr, .col (the packed layout of khcore_batch_create)."""
+    ns = np.array([g.n for g in graphs], dtype=np.int64)
+    ms = np.array([len(g.col) for g in graphs], dtype=np.int64)
+    v_off = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
+    e_off = np.concatenate([[0], np.cumsum(ms)]).astype(np.int64)
+    rp = np.concatenate([np.asarray(g.row_ptr, dtype=np.int32) for g in graphs]) if graphs else np.zeros(0, np.int32)
+    col = np.concatenate([np.asarray(g.col, dtype=np.int32) for g in graphs]) if graphs else np.zeros(0, np.int32)
+    return v_off, e_off, rp, col
 
 
 class KHCore:

@@ -1,11 +1,13 @@
 // khcore_api.cu — the C ABI declared in include/khcore.h: context life cycle,
-// CSR validation, and the host side of the level-synchronous peeler.
+// CSR validation, and the host side of the level-synchronous peeler for one
+// graph or a batch of disjoint graphs.
 #include <algorithm>
 #include <climits>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -18,6 +20,8 @@ using namespace khc;
 struct khcore_ctx {
     int32_t n = 0;
     int64_t m = 0;
+    int32_t G = 1;                // graphs held (1 for khcore_create)
+    std::vector<int64_t> v_off;   // [G+1] vertex offsets of the graphs
     int device = 0;
     int sm_count = 0;
     cudaStream_t stream = nullptr;
@@ -29,14 +33,20 @@ struct khcore_ctx {
     int32_t *row_ptr = nullptr, *col = nullptr;
     int32_t *classes = nullptr;  // light | medium | heavy lists, back to back
     int32_t n_light = 0, n_medium = 0, n_heavy = 0;
+    int32_t *gid = nullptr;      // [n] graph of each vertex (G > 1 only)
+
+    // per-graph peel parameters (device)
+    int32_t *kg = nullptr, *ming = nullptr, *hg = nullptr, *gcls = nullptr;
+    int32_t *cls_off = nullptr, *nAc = nullptr;  // [G] capacity each (ncls <= G)
+    int32_t *cls_src = nullptr;                  // [n] vertices grouped by h-class
 
     // peel state (device)
     uint32_t *alive = nullptr;
     int32_t *deg = nullptr, *core = nullptr, *rnd = nullptr, *src = nullptr;
-    uint32_t *aff[2] = {nullptr, nullptr};
     uint32_t *vis = nullptr;
     PeelState *st = nullptr;
     PeelState *st_host = nullptr;  // pinned mirror
+    int32_t *nAc_host = nullptr;   // pinned mirror of nAc
 
     // BFS buffers, sized for W_alloc words per vertex
     int W_req = 0;  // 0 = automatic
@@ -48,8 +58,8 @@ struct khcore_ctx {
     int32_t *T = nullptr;
     LevelCtl *ctl = nullptr;
     int32_t *cnt = nullptr;
-    int32_t push_alpha = 16;  // push when frontier degree sum * alpha < alive CSR entries
     unsigned long long *edges = nullptr;  // device counter of plain-BFS-equivalent edges
+    int32_t push_alpha = 16;              // push when frontier degree sum * alpha < alive CSR entries
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
@@ -97,16 +107,16 @@ khcore_status fail(khcore_ctx *c, khcore_status s, const char *fmt, ...)
     return s;
 }
 
-#define CU(call)                                                                            \
-    do {                                                                                    \
-        cudaError_t e_ = (call);                                                            \
-        if (e_ != cudaSuccess) {                                                            \
-            if (e_ == cudaErrorMemoryAllocation) {                                          \
-                (void)cudaGetLastError();                                                   \
-                return fail(c, KHCORE_ENOMEM, "%s: %s", #call, cudaGetErrorString(e_));     \
-            }                                                                               \
-            return fail(c, KHCORE_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));          \
-        }                                                                                   \
+#define CU(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            if (e_ == cudaErrorMemoryAllocation) {                                      \
+                (void)cudaGetLastError();                                               \
+                return fail(c, KHCORE_ENOMEM, "%s: %s", #call, cudaGetErrorString(e_)); \
+            }                                                                           \
+            return fail(c, KHCORE_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));      \
+        }                                                                               \
     } while (0)
 
 bool is_device_ptr(const void *p)
@@ -246,9 +256,10 @@ khcore_status flush_timer(khcore_ctx *c)
 }
 
 // h-degrees of the sources src[0..ns) in G[alive], in batches of 64*W.
-// n_b / m_b: alive rows and their CSR entries (for the algorithmic bytes).
-khcore_status hdeg_sources(khcore_ctx *c, int W, int32_t h, int32_t ns, int64_t n_b, int64_t m_b,
-                           khcore_stats *stt)
+// n_b / m_b: alive rows and their CSR entries (direction choice and
+// algorithmic bytes).
+khcore_status hdeg_sources(khcore_ctx *c, int W, int32_t h, const int32_t *src, int32_t ns, int64_t n_b,
+                           int64_t m_b, khcore_stats *stt)
 {
     const GraphView g = c->view();
     BfsBufs b;
@@ -276,7 +287,7 @@ khcore_status hdeg_sources(khcore_ctx *c, int W, int32_t h, int32_t ns, int64_t 
             khcore_status s = flush_timer(c);
             if (s != KHCORE_OK) return s;
         }
-        CU(run_bfs_batch(W, g, c->alive, b, c->src + off, cur, h, c->deg, tune, grid, c->stream,
+        CU(run_bfs_batch(W, g, c->alive, b, src + off, cur, h, c->deg, tune, grid, c->stream,
                          stt ? &stt->kernel_launches : nullptr, c->profiling ? &c->timer : nullptr));
         if (stt) {
             stt->source_batches++;
@@ -304,7 +315,277 @@ khcore_status write_out(khcore_ctx *c, int32_t *dst, const int32_t *src_dev)
     return KHCORE_OK;
 }
 
-int32_t effective_h(int32_t n, int32_t h) { return std::min(h, std::max(n - 1, 1)); }
+// h > n-1 behaves as n-1 (no distance exceeds it).
+int32_t effective_h(int64_t n, int32_t h) { return (int32_t)std::min<int64_t>(h, std::max<int64_t>(n - 1, 1)); }
+
+// Upload a validated global CSR and set up every device buffer.
+khcore_status setup_ctx(khcore_ctx *c, const std::vector<int32_t> &rp, const std::vector<int32_t> &col,
+                        const std::vector<int32_t> *gid_host, void *stream)
+{
+    const int32_t n = c->n;
+    const int64_t m = c->m;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) return fail(nullptr, KHCORE_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return fail(nullptr, KHCORE_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+        c->own_stream = true;
+    }
+    // degree classes of the pull direction
+    std::vector<int32_t> classes;
+    classes.reserve(n);
+    for (int pass = 0; pass < 3; pass++)
+        for (int32_t v = 0; v < n; v++) {
+            const int32_t d = rp[v + 1] - rp[v];
+            const int cls = d <= kLightMax ? 0 : (d <= kMediumMax ? 1 : 2);
+            if (cls == pass) classes.push_back(v);
+        }
+    for (int32_t v = 0; v < n; v++) {
+        const int32_t d = rp[v + 1] - rp[v];
+        if (d <= kLightMax) c->n_light++;
+        else if (d <= kMediumMax) c->n_medium++;
+        else c->n_heavy++;
+    }
+    const size_t nw = ((size_t)n + 31) / 32;
+    const size_t nflag = (((size_t)n + 3) / 4) * 4;  // whole 32-bit words (flag claims)
+    khcore_status st = KHCORE_OK;
+    auto A = [&](cudaError_t e2) {
+        if (e2 != cudaSuccess && st == KHCORE_OK) {
+            (void)cudaGetLastError();
+            st = fail(nullptr, e2 == cudaErrorMemoryAllocation ? KHCORE_ENOMEM : KHCORE_ECUDA, "device allocation: %s",
+                      cudaGetErrorString(e2));
+        }
+    };
+    A(dev_alloc(&c->row_ptr, (size_t)n + 1));
+    A(dev_alloc(&c->col, (size_t)m));
+    A(dev_alloc(&c->classes, (size_t)n));
+    A(dev_alloc(&c->alive, nw));
+    A(dev_alloc(&c->deg, (size_t)n));
+    A(dev_alloc(&c->core, (size_t)n));
+    A(dev_alloc(&c->rnd, (size_t)n));
+    A(dev_alloc(&c->src, (size_t)n));
+    A(dev_alloc(&c->cls_src, (size_t)n));
+    A(dev_alloc(&c->vis, nw));
+    A(dev_alloc(&c->st, 1));
+    A(dev_alloc(&c->edges, 1));
+    A(dev_alloc(&c->flag[0], nflag));
+    A(dev_alloc(&c->flag[1], nflag));
+    for (int k = 0; k < 3; k++) {
+        A(dev_alloc(&c->Q[k], (size_t)n));
+        A(dev_alloc(&c->QH[k], (size_t)n));
+    }
+    A(dev_alloc(&c->T, (size_t)n));
+    A(dev_alloc(&c->ctl, 1));
+    A(dev_alloc(&c->kg, (size_t)c->G));
+    A(dev_alloc(&c->ming, (size_t)c->G));
+    A(dev_alloc(&c->hg, (size_t)c->G));
+    A(dev_alloc(&c->gcls, (size_t)c->G));
+    A(dev_alloc(&c->cls_off, (size_t)c->G));
+    A(dev_alloc(&c->nAc, (size_t)c->G));
+    if (c->G > 1) A(dev_alloc(&c->gid, (size_t)n));
+    if (st != KHCORE_OK) return st;
+    e = cudaMallocHost((void **)&c->st_host, sizeof(PeelState));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->nAc_host, sizeof(int32_t) * (size_t)c->G);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->row_ptr, rp.data(), ((size_t)n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice,
+                            c->stream);
+    if (e == cudaSuccess && m)
+        e = cudaMemcpyAsync(c->col, col.data(), (size_t)m * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && n)
+        e = cudaMemcpyAsync(c->classes, classes.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice,
+                            c->stream);
+    if (e == cudaSuccess && gid_host && n)
+        e = cudaMemcpyAsync(c->gid, gid_host->data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->flag[0], 0, nflag, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->flag[1], 0, nflag, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(nullptr, KHCORE_ECUDA, "graph upload: %s", cudaGetErrorString(e));
+    return KHCORE_OK;
+}
+
+// The decomposition driver. h_in[g] is the hop bound of graph g (g < c->G).
+khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t *core_out, int32_t *round_out,
+                        khcore_stats *stats)
+{
+    khcore_stats stt;
+    std::memset(&stt, 0, sizeof stt);
+    const int32_t G = c->G;
+    // effective h per graph, h-classes (graphs with equal h), class regions
+    std::vector<int32_t> hg(G), gcls(G);
+    std::map<int32_t, int32_t> cls_of_h;
+    int32_t hmax = 1;
+    for (int32_t g = 0; g < G; g++) {
+        hg[g] = effective_h(c->v_off[g + 1] - c->v_off[g], h_in[g]);
+        hmax = std::max(hmax, hg[g]);
+    }
+    for (int32_t g = 0; g < G; g++) cls_of_h.emplace(hg[g], 0);
+    std::vector<int32_t> cls_h;
+    for (auto &kv : cls_of_h) {
+        kv.second = (int32_t)cls_h.size();
+        cls_h.push_back(kv.first);
+    }
+    const int32_t ncls = (int32_t)cls_h.size();
+    std::vector<int64_t> cls_size(ncls, 0);
+    for (int32_t g = 0; g < G; g++) {
+        gcls[g] = cls_of_h[hg[g]];
+        cls_size[gcls[g]] += c->v_off[g + 1] - c->v_off[g];
+    }
+    std::vector<int32_t> cls_off(ncls), cls_src((size_t)c->n);
+    {
+        int64_t o = 0;
+        for (int32_t k = 0; k < ncls; k++) {
+            cls_off[k] = (int32_t)o;
+            o += cls_size[k];
+        }
+        std::vector<int64_t> fill(cls_off.begin(), cls_off.end());
+        for (int32_t g = 0; g < G; g++)
+            for (int64_t v = c->v_off[g]; v < c->v_off[g + 1]; v++) cls_src[fill[gcls[g]]++] = (int32_t)v;
+    }
+    stt.h = G == 1 ? hg[0] : hmax;
+    if (c->n == 0) {
+        if (stats) *stats = stt;
+        return KHCORE_OK;
+    }
+    const int W = c->W_req ? c->W_req : auto_words(c->n);
+    stt.words_per_vertex = W;
+    khcore_status s;
+    if ((s = ensure_bfs(c, W)) != KHCORE_OK) return s;
+    const GraphView g = c->view();
+    const int grid = bfs_grid(c, W);
+    const size_t nwb = (((size_t)c->n + 31) / 32) * sizeof(uint32_t);
+
+    PeelView pv;
+    pv.G = G;
+    pv.ncls = ncls;
+    pv.gid = c->G > 1 ? c->gid : nullptr;
+    pv.kg = c->kg;
+    pv.ming = c->ming;
+    pv.hg = c->hg;
+    pv.cls = c->gcls;
+    pv.cls_off = c->cls_off;
+    pv.nAc = c->nAc;
+
+    CU(cudaEventRecord(c->ev0, c->stream));
+    PeelState init;
+    std::memset(&init, 0, sizeof init);
+    init.alive = c->n;
+    init.m_alive = (unsigned long long)c->m;
+    *c->st_host = init;
+    c->level_ms = 0.0;
+    c->level_launches = 0;
+    c->timer.used = 0;
+    std::vector<int32_t> ming_init(G, INT_MAX);
+    CU(cudaMemcpyAsync(c->st, c->st_host, sizeof(PeelState), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemsetAsync(c->kg, 0, sizeof(int32_t) * G, c->stream));
+    CU(cudaMemcpyAsync(c->ming, ming_init.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->hg, hg.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->gcls, gcls.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->cls_off, cls_off.data(), sizeof(int32_t) * ncls, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->cls_src, cls_src.data(), sizeof(int32_t) * c->n, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemsetAsync(c->edges, 0, sizeof(unsigned long long), c->stream));
+    CU(launch_alive_init(c->alive, c->n, c->stream));
+    stt.kernel_launches += 1;
+    // the host vectors above must outlive the async copies
+    CU(cudaStreamSynchronize(c->stream));
+
+    // initial h-degrees, class by class
+    for (int32_t k = 0; k < ncls; k++)
+        if ((s = hdeg_sources(c, W, cls_h[k], c->cls_src + cls_off[k], (int32_t)cls_size[k], c->n, c->m, &stt)) !=
+            KHCORE_OK)
+            return s;
+
+    // KHCORE_TRACE=1 prints one line per peel round to stderr (tracing aid)
+    const char *trace_env = getenv("KHCORE_TRACE");
+    const bool trace = trace_env && trace_env[0] == '1';
+    int32_t round = 0;
+    for (;;) {
+        // one round: levels, peel sets D, affected sets A, recompute deg[A];
+        // the affected-BFS frontier lists reuse the BFS frontier lists Q[0..2]
+        CU(launch_min_alive_deg(g, c->alive, c->deg, pv, grid, c->stream));
+        CU(launch_set_level(pv, c->st, c->stream));
+        CU(cudaMemsetAsync(c->vis, 0, nwb, c->stream));
+        CU(launch_peel_compact(g, c->alive, c->deg, pv, c->st, c->core, c->rnd, c->vis, c->Q[0], grid, c->stream));
+        stt.kernel_launches += 3;
+        for (int lvl = 0; lvl < hmax; lvl++) {
+            CU(launch_affected_level(g, c->alive, lvl, c->Q, c->vis, pv, c->st, c->src, lvl == hmax - 1, grid,
+                                     c->stream));
+            stt.kernel_launches++;
+        }
+        CU(launch_sum_classes(pv, c->st, c->stream));
+        stt.kernel_launches++;
+        CU(cudaMemcpyAsync(c->st_host, c->st, sizeof(PeelState), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaMemcpyAsync(c->nAc_host, c->nAc, sizeof(int32_t) * ncls, cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        const PeelState ps = *c->st_host;
+        if (ps.nD <= 0)
+            return fail(c, KHCORE_EINTERNAL, "round %d deleted no vertex with %d alive", round, ps.alive);
+        stt.deleted_total += ps.nD;
+        stt.affected_total += ps.nA;
+        if (trace) {
+            float tms = 0.f;
+            cudaEventRecord(c->ev1, c->stream);
+            cudaEventSynchronize(c->ev1);
+            cudaEventElapsedTime(&tms, c->ev0, c->ev1);
+            fprintf(stderr, "khcore round %d: |D|=%d |A|=%d alive=%d m_alive=%llu t=%.1f ms\n", round, ps.nD, ps.nA,
+                    ps.alive, (unsigned long long)ps.m_alive, tms);
+        }
+        round++;
+        if (ps.alive == 0) break;
+        for (int32_t k = 0; k < ncls; k++) {
+            const int32_t na = c->nAc_host[k];
+            if (na > 0 && (s = hdeg_sources(c, W, cls_h[k], c->src + cls_off[k], na, ps.alive, (int64_t)ps.m_alive,
+                                            &stt)) != KHCORE_OK)
+                return s;
+        }
+        // advance the device-side round counter
+        c->st_host->round = round;
+        CU(cudaMemcpyAsync(&c->st->round, &c->st_host->round, sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    }
+    stt.rounds = round;
+    CU(cudaEventRecord(c->ev1, c->stream));
+    if ((s = write_out(c, core_out, c->core)) != KHCORE_OK) return s;
+    if ((s = write_out(c, round_out, c->rnd)) != KHCORE_OK) return s;
+    unsigned long long edges = 0;
+    std::vector<int32_t> kg(G);
+    CU(cudaMemcpyAsync(&edges, c->edges, sizeof edges, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(kg.data(), c->kg, sizeof(int32_t) * G, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    stt.device_ms = ms;
+    stt.edges_traversed = (int64_t)edges;
+    stt.k_max = *std::max_element(kg.begin(), kg.end());
+    if ((s = flush_timer(c)) != KHCORE_OK) return s;
+    stt.level_ms = c->level_ms;
+    stt.level_launches = c->level_launches;
+    if (!c->profiling) stt.level_bytes = 0;
+    if (stats) *stats = stt;
+    return KHCORE_OK;
+}
+
+khcore_status create_common(int32_t G, const std::vector<int64_t> &v_off, std::vector<int32_t> &rp,
+                            std::vector<int32_t> &cl, const std::vector<int32_t> *gid, void *stream,
+                            khcore_ctx **out)
+{
+    khcore_ctx *c = new (std::nothrow) khcore_ctx();
+    if (!c) return fail(nullptr, KHCORE_ENOMEM, "host allocation failed");
+    c->n = (int32_t)v_off[G];
+    c->m = rp[c->n];
+    c->G = G;
+    c->v_off = v_off;
+    khcore_status st = setup_ctx(c, rp, cl, gid, stream);
+    if (st != KHCORE_OK) {
+        khcore_destroy(c);
+        return st;
+    }
+    *out = c;
+    return KHCORE_OK;
+}
 
 }  // namespace
 
@@ -328,39 +609,21 @@ const char *khcore_last_error(const khcore_ctx *ctx) { return ctx ? ctx->err.c_s
 
 int32_t khcore_num_vertices(const khcore_ctx *ctx) { return ctx ? ctx->n : 0; }
 int64_t khcore_num_entries(const khcore_ctx *ctx) { return ctx ? ctx->m : 0; }
+int32_t khcore_num_graphs(const khcore_ctx *ctx) { return ctx ? ctx->G : 0; }
 
 void khcore_destroy(khcore_ctx *c)
 {
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->stream && !c->failed) cudaStreamSynchronize(c->stream);
-    cudaFree(c->row_ptr);
-    cudaFree(c->col);
-    cudaFree(c->classes);
-    cudaFree(c->alive);
-    cudaFree(c->deg);
-    cudaFree(c->core);
-    cudaFree(c->rnd);
-    cudaFree(c->src);
-    cudaFree(c->aff[0]);
-    cudaFree(c->aff[1]);
-    cudaFree(c->vis);
-    cudaFree(c->st);
-    cudaFree(c->V);
-    cudaFree(c->F[0]);
-    cudaFree(c->F[1]);
-    cudaFree(c->flag[0]);
-    cudaFree(c->flag[1]);
-    for (int k = 0; k < 3; k++) {
-        cudaFree(c->Q[k]);
-        cudaFree(c->QH[k]);
-    }
-    cudaFree(c->T);
-    cudaFree(c->ctl);
-    cudaFree(c->cnt);
-    cudaFree(c->edges);
+    void *bufs[] = {c->row_ptr, c->col, c->classes, c->gid, c->kg, c->ming, c->hg, c->gcls, c->cls_off, c->nAc,
+                    c->cls_src, c->alive, c->deg, c->core, c->rnd, c->src, c->vis, c->st, c->V, c->F[0], c->F[1],
+                    c->flag[0], c->flag[1], c->Q[0], c->Q[1], c->Q[2], c->QH[0], c->QH[1], c->QH[2], c->T, c->ctl,
+                    c->cnt, c->edges};
+    for (void *p : bufs) cudaFree(p);
     for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
     if (c->st_host) cudaFreeHost(c->st_host);
+    if (c->nAc_host) cudaFreeHost(c->nAc_host);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -371,15 +634,13 @@ void khcore_destroy(khcore_ctx *c)
 khcore_status khcore_create(int32_t n, const int32_t *row_ptr, const int32_t *col, uint32_t flags, void *stream,
                             khcore_ctx **out)
 {
-    khcore_ctx *c = nullptr;
     if (!out) return fail(nullptr, KHCORE_EINVAL, "out is NULL");
     *out = nullptr;
     if (n < 0) return fail(nullptr, KHCORE_EINVAL, "n must be >= 0 (got %d)", n);
     if (!row_ptr) return fail(nullptr, KHCORE_EINVAL, "row_ptr is NULL");
 
     std::vector<int32_t> rp, cl, sorted;
-    if (fetch(rp, row_ptr, (size_t)n + 1) != cudaSuccess)
-        return fail(nullptr, KHCORE_ECUDA, "cannot read row_ptr");
+    if (fetch(rp, row_ptr, (size_t)n + 1) != cudaSuccess) return fail(nullptr, KHCORE_ECUDA, "cannot read row_ptr");
     const int64_t m = rp[n];
     if (m < 0) return fail(nullptr, KHCORE_EINVAL, "row_ptr[n] is negative");
     if (m > 0 && !col) return fail(nullptr, KHCORE_EINVAL, "col is NULL but row_ptr[n] = %lld", (long long)m);
@@ -390,100 +651,59 @@ khcore_status khcore_create(int32_t n, const int32_t *row_ptr, const int32_t *co
     } else {
         sorted.swap(cl);
     }
+    std::vector<int64_t> v_off = {0, n};
+    return create_common(1, v_off, rp, sorted, nullptr, stream, out);
+}
 
-    c = new (std::nothrow) khcore_ctx();
-    if (!c) return fail(nullptr, KHCORE_ENOMEM, "host allocation failed");
-    c->n = n;
-    c->m = m;
-    khcore_status st = KHCORE_OK;
-    do {
-        cudaError_t e = cudaGetDevice(&c->device);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
-        if (e != cudaSuccess) {
-            st = fail(nullptr, KHCORE_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
-            break;
-        }
-        if (stream) {
-            c->stream = (cudaStream_t)stream;
+khcore_status khcore_batch_create(int32_t G, const int64_t *v_off, const int64_t *e_off, const int32_t *row_ptr_local,
+                                  const int32_t *col_local, uint32_t flags, void *stream, khcore_ctx **out)
+{
+    if (!out) return fail(nullptr, KHCORE_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (G < 1) return fail(nullptr, KHCORE_EINVAL, "G must be >= 1 (got %d)", G);
+    if (!v_off || !e_off || !row_ptr_local) return fail(nullptr, KHCORE_EINVAL, "NULL offset or row_ptr array");
+    std::vector<int64_t> vo, eo;
+    if (fetch(vo, v_off, (size_t)G + 1) != cudaSuccess || fetch(eo, e_off, (size_t)G + 1) != cudaSuccess)
+        return fail(nullptr, KHCORE_ECUDA, "cannot read offsets");
+    if (vo[0] != 0 || eo[0] != 0) return fail(nullptr, KHCORE_EINVAL, "v_off[0] and e_off[0] must be 0");
+    for (int32_t g = 0; g < G; g++)
+        if (vo[g + 1] < vo[g] || eo[g + 1] < eo[g])
+            return fail(nullptr, KHCORE_EINVAL, "offsets decrease at graph %d", g);
+    if (vo[G] > INT32_MAX || eo[G] > INT32_MAX)
+        return fail(nullptr, KHCORE_EINVAL, "batch too large for int32 ids (%lld vertices, %lld entries)",
+                    (long long)vo[G], (long long)eo[G]);
+    const int32_t n = (int32_t)vo[G];
+    const int64_t m = eo[G];
+    std::vector<int32_t> rpl, cll;
+    if (fetch(rpl, row_ptr_local, (size_t)n + G) != cudaSuccess)
+        return fail(nullptr, KHCORE_ECUDA, "cannot read row_ptr");
+    if (m > 0 && !col_local) return fail(nullptr, KHCORE_EINVAL, "col_local is NULL");
+    if (fetch(cll, col_local, (size_t)m) != cudaSuccess) return fail(nullptr, KHCORE_ECUDA, "cannot read col");
+    // the union graph: global ids, one CSR; each graph validated on its own
+    std::vector<int32_t> rp((size_t)n + 1), cl((size_t)m), gid((size_t)n);
+    for (int32_t g = 0; g < G; g++) {
+        const int32_t ng = (int32_t)(vo[g + 1] - vo[g]);
+        const int64_t mg = eo[g + 1] - eo[g];
+        const int32_t *lrp = rpl.data() + vo[g] + g;
+        if (lrp[ng] != mg)
+            return fail(nullptr, KHCORE_EINVAL, "graph %d: row_ptr[n_g] = %d but e_off gives %lld entries", g,
+                        lrp[ng], (long long)mg);
+        std::vector<int32_t> lr(lrp, lrp + ng + 1), lc(cll.begin() + eo[g], cll.begin() + eo[g + 1]), ls;
+        if (!(flags & KHCORE_FLAG_TRUST_INPUT)) {
+            std::string msg;
+            if (!validate_csr(ng, lr, lc, ls, msg))
+                return fail(nullptr, KHCORE_EINVAL, "graph %d: invalid CSR: %s", g, msg.c_str());
         } else {
-            e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
-            if (e != cudaSuccess) {
-                st = fail(nullptr, KHCORE_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
-                break;
-            }
-            c->own_stream = true;
+            ls.swap(lc);
         }
-        // degree classes
-        std::vector<int32_t> classes;
-        classes.reserve(n);
-        for (int pass = 0; pass < 3; pass++)
-            for (int32_t v = 0; v < n; v++) {
-                const int32_t d = rp[v + 1] - rp[v];
-                const int cls = d <= kLightMax ? 0 : (d <= kMediumMax ? 1 : 2);
-                if (cls == pass) classes.push_back(v);
-            }
-        for (int32_t v = 0; v < n; v++) {
-            const int32_t d = rp[v + 1] - rp[v];
-            if (d <= kLightMax) c->n_light++;
-            else if (d <= kMediumMax) c->n_medium++;
-            else c->n_heavy++;
+        for (int32_t i = 0; i < ng; i++) {
+            rp[vo[g] + i] = (int32_t)(eo[g] + lr[i]);
+            gid[vo[g] + i] = g;
         }
-        const size_t nw = ((size_t)n + 31) / 32;
-        auto A = [&](cudaError_t e2) {
-            if (e2 != cudaSuccess && st == KHCORE_OK) {
-                (void)cudaGetLastError();
-                st = fail(nullptr, e2 == cudaErrorMemoryAllocation ? KHCORE_ENOMEM : KHCORE_ECUDA,
-                          "device allocation: %s", cudaGetErrorString(e2));
-            }
-        };
-        A(dev_alloc(&c->row_ptr, (size_t)n + 1));
-        A(dev_alloc(&c->col, (size_t)m));
-        A(dev_alloc(&c->classes, (size_t)n));
-        A(dev_alloc(&c->alive, nw));
-        A(dev_alloc(&c->deg, (size_t)n));
-        A(dev_alloc(&c->core, (size_t)n));
-        A(dev_alloc(&c->rnd, (size_t)n));
-        A(dev_alloc(&c->src, (size_t)n));
-        A(dev_alloc(&c->aff[0], nw));
-        A(dev_alloc(&c->aff[1], nw));
-        A(dev_alloc(&c->vis, nw));
-        A(dev_alloc(&c->st, 1));
-        A(dev_alloc(&c->edges, 1));
-        const size_t nflag = (((size_t)n + 3) / 4) * 4;  // whole 32-bit words (flag claims)
-        A(dev_alloc(&c->flag[0], nflag));
-        A(dev_alloc(&c->flag[1], nflag));
-        for (int k = 0; k < 3; k++) {
-            A(dev_alloc(&c->Q[k], (size_t)n));
-            A(dev_alloc(&c->QH[k], (size_t)n));
-        }
-        A(dev_alloc(&c->T, (size_t)n));
-        A(dev_alloc(&c->ctl, 1));
-        if (st != KHCORE_OK) break;
-        e = cudaMallocHost((void **)&c->st_host, sizeof(PeelState));
-        if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
-        if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(c->row_ptr, rp.data(), ((size_t)n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice,
-                                c->stream);
-        if (e == cudaSuccess && m)
-            e = cudaMemcpyAsync(c->col, sorted.data(), (size_t)m * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream);
-        if (e == cudaSuccess && n)
-            e = cudaMemcpyAsync(c->classes, classes.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice,
-                                c->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(c->flag[0], 0, nflag, c->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(c->flag[1], 0, nflag, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) {
-            st = fail(nullptr, KHCORE_ECUDA, "graph upload: %s", cudaGetErrorString(e));
-            break;
-        }
-    } while (0);
-    if (st != KHCORE_OK) {
-        khcore_destroy(c);
-        return st;
+        for (int64_t k = 0; k < mg; k++) cl[eo[g] + k] = (int32_t)(vo[g] + ls[k]);
     }
-    *out = c;
-    return KHCORE_OK;
+    rp[n] = (int32_t)m;
+    return create_common(G, vo, rp, cl, &gid, stream, out);
 }
 
 khcore_status khcore_set_words(khcore_ctx *c, int32_t words)
@@ -530,10 +750,12 @@ khcore_status khcore_hdegrees(khcore_ctx *c, int32_t h, int32_t *deg_out)
     if (c->n == 0) return KHCORE_OK;
     const int W = c->W_req ? c->W_req : auto_words(c->n);
     if ((s = ensure_bfs(c, W)) != KHCORE_OK) return s;
-    const int32_t he = effective_h(c->n, h);
+    int32_t hmax = 1;
+    for (int32_t g = 0; g < c->G; g++) hmax = std::max(hmax, effective_h(c->v_off[g + 1] - c->v_off[g], h));
     CU(launch_alive_init(c->alive, c->n, c->stream));
     CU(launch_iota(c->src, c->n, c->stream));
-    if ((s = hdeg_sources(c, W, he, c->n, c->n, c->m, nullptr)) != KHCORE_OK) return s;
+    // graphs are disjoint: one BFS over the union gives every graph's h-degrees
+    if ((s = hdeg_sources(c, W, hmax, c->src, c->n, c->n, c->m, nullptr)) != KHCORE_OK) return s;
     if ((s = write_out(c, deg_out, c->deg)) != KHCORE_OK) return s;
     CU(cudaStreamSynchronize(c->stream));
     return KHCORE_OK;
@@ -546,104 +768,26 @@ khcore_status khcore_decompose_ex(khcore_ctx *c, int32_t h, int32_t *core_out, i
     if (s != KHCORE_OK) return s;
     if (h < 1) return fail(c, KHCORE_EINVAL, "h must be >= 1 (got %d)", h);
     if (!core_out && c->n) return fail(c, KHCORE_EINVAL, "core_out is NULL");
-    khcore_stats stt;
-    std::memset(&stt, 0, sizeof stt);
-    const int32_t he = c->n ? effective_h(c->n, h) : h;
-    stt.h = he;
-    if (c->n == 0) {
-        if (stats) *stats = stt;
-        return KHCORE_OK;
-    }
-    const int W = c->W_req ? c->W_req : auto_words(c->n);
-    stt.words_per_vertex = W;
-    if ((s = ensure_bfs(c, W)) != KHCORE_OK) return s;
-    const GraphView g = c->view();
-    const int grid = bfs_grid(c, W);
-    const size_t nwb = (((size_t)c->n + 31) / 32) * sizeof(uint32_t);
-
-    CU(cudaEventRecord(c->ev0, c->stream));
-    // initial state: everything alive, k = 0, all h-degrees
-    PeelState init;
-    std::memset(&init, 0, sizeof init);
-    init.min_deg = INT_MAX;
-    init.alive = c->n;
-    init.m_alive = (unsigned long long)c->m;
-    *c->st_host = init;
-    c->level_ms = 0.0;
-    c->level_launches = 0;
-    c->timer.used = 0;
-    CU(cudaMemcpyAsync(c->st, c->st_host, sizeof(PeelState), cudaMemcpyHostToDevice, c->stream));
-    CU(cudaMemsetAsync(c->edges, 0, sizeof(unsigned long long), c->stream));
-    CU(launch_alive_init(c->alive, c->n, c->stream));
-    CU(launch_iota(c->src, c->n, c->stream));
-    stt.kernel_launches += 2;
-    if ((s = hdeg_sources(c, W, he, c->n, c->n, c->m, &stt)) != KHCORE_OK) return s;
-
-    // KHCORE_TRACE=1 prints one line per peel round to stderr (tracing aid)
-    const char *trace_env = getenv("KHCORE_TRACE");
-    const bool trace = trace_env && trace_env[0] == '1';
-    int32_t round = 0;
-    for (;;) {
-        // one round: level, peel set D, affected set A, recompute deg[A]
-        CU(launch_min_alive_deg(g, c->alive, c->deg, c->st, grid, c->stream));
-        CU(launch_set_level(c->st, c->stream));
-        CU(cudaMemsetAsync(c->aff[0], 0, nwb, c->stream));
-        CU(cudaMemsetAsync(c->vis, 0, nwb, c->stream));
-        CU(launch_peel_compact(g, c->alive, c->deg, c->st, c->core, c->rnd, c->aff[0], grid, c->stream));
-        stt.kernel_launches += 3;
-        for (int lvl = 0; lvl < he; lvl++) {
-            CU(cudaMemsetAsync(c->aff[(lvl + 1) & 1], 0, nwb, c->stream));
-            CU(launch_affected_level(g, c->alive, c->aff[lvl & 1], c->aff[(lvl + 1) & 1], c->vis, grid, c->stream));
-            stt.kernel_launches++;
-        }
-        CU(launch_compact_affected(g, c->alive, c->vis, c->st, c->src, grid, c->stream));
-        stt.kernel_launches++;
-        CU(cudaMemcpyAsync(c->st_host, c->st, sizeof(PeelState), cudaMemcpyDeviceToHost, c->stream));
-        CU(cudaStreamSynchronize(c->stream));
-        const PeelState ps = *c->st_host;
-        if (ps.nD <= 0)
-            return fail(c, KHCORE_EINTERNAL, "round %d deleted no vertex with %d alive", round, ps.alive);
-        stt.deleted_total += ps.nD;
-        stt.affected_total += ps.nA;
-        if (trace) {
-            float tms = 0.f;
-            cudaEventRecord(c->ev1, c->stream);
-            cudaEventSynchronize(c->ev1);
-            cudaEventElapsedTime(&tms, c->ev0, c->ev1);
-            fprintf(stderr, "khcore round %d: k=%d |D|=%d |A|=%d alive=%d m_alive=%llu t=%.1f ms\n", round,
-                    ps.k, ps.nD, ps.nA, ps.alive, (unsigned long long)ps.m_alive, tms);
-        }
-        stt.k_max = ps.k;
-        round++;
-        if (ps.alive == 0) break;
-        if (ps.nA > 0 && (s = hdeg_sources(c, W, he, ps.nA, ps.alive, (int64_t)ps.m_alive, &stt)) != KHCORE_OK)
-            return s;
-        // advance the device-side round counter
-        c->st_host->round = round;
-        CU(cudaMemcpyAsync(&c->st->round, &c->st_host->round, sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
-    }
-    stt.rounds = round;
-    CU(cudaEventRecord(c->ev1, c->stream));
-    if ((s = write_out(c, core_out, c->core)) != KHCORE_OK) return s;
-    if ((s = write_out(c, round_out, c->rnd)) != KHCORE_OK) return s;
-    unsigned long long edges = 0;
-    CU(cudaMemcpyAsync(&edges, c->edges, sizeof edges, cudaMemcpyDeviceToHost, c->stream));
-    CU(cudaStreamSynchronize(c->stream));
-    float ms = 0.f;
-    CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
-    stt.device_ms = ms;
-    stt.edges_traversed = (int64_t)edges;
-    if ((s = flush_timer(c)) != KHCORE_OK) return s;
-    stt.level_ms = c->level_ms;
-    stt.level_launches = c->level_launches;
-    if (!c->profiling) stt.level_bytes = 0;
-    if (stats) *stats = stt;
-    return KHCORE_OK;
+    return decompose(c, std::vector<int32_t>((size_t)c->G, h), core_out, round_out, stats);
 }
 
 khcore_status khcore_decompose(khcore_ctx *c, int32_t h, int32_t *core_out)
 {
     return khcore_decompose_ex(c, h, core_out, nullptr, nullptr);
+}
+
+khcore_status khcore_batch_decompose(khcore_ctx *c, const int32_t *h, int32_t *core_out, int32_t *round_out,
+                                     khcore_stats *stats)
+{
+    khcore_status s = check_ctx(c);
+    if (s != KHCORE_OK) return s;
+    if (!h) return fail(c, KHCORE_EINVAL, "h is NULL");
+    if (!core_out && c->n) return fail(c, KHCORE_EINVAL, "core_out is NULL");
+    std::vector<int32_t> hv;
+    if (fetch(hv, h, (size_t)c->G) != cudaSuccess) return fail(c, KHCORE_ECUDA, "cannot read h");
+    for (int32_t g = 0; g < c->G; g++)
+        if (hv[g] < 1) return fail(c, KHCORE_EINVAL, "h[%d] must be >= 1 (got %d)", g, hv[g]);
+    return decompose(c, hv, core_out, round_out, stats);
 }
 
 }  // extern "C"

@@ -155,6 +155,69 @@ __device__ __forceinline__ void append_frontier(bool pred, int32_t y, int32_t de
     if (pred) acc.fe += (unsigned long long)deg;
 }
 
+
+// OR the W words of frontier row x into a.
+template <int W>
+__device__ __forceinline__ void or_row(uint64_t (&a)[W], const uint64_t *__restrict__ F, int32_t x)
+{
+    if constexpr (W == 1) {
+        a[0] |= __ldg(F + x);
+    } else {
+        const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(F + (size_t)x * W);
+#pragma unroll
+        for (int k = 0; k < W / 2; k++) {
+            const ulonglong2 v = __ldg(p + k);
+            a[2 * k] |= v.x;
+            a[2 * k + 1] |= v.y;
+        }
+    }
+}
+
+// Edges e = first, first+stride, ... < e1: OR the rows of flagged neighbours
+// into a. Two edges per step so that each lane keeps two independent
+// col -> flag -> row chains in flight.
+template <int W>
+__device__ __forceinline__ void gather_edges(uint64_t (&a)[W], const int32_t *__restrict__ col,
+                                             const uint8_t *__restrict__ flc, const uint64_t *__restrict__ Fc,
+                                             int32_t first, int32_t e1, int32_t stride)
+{
+    int32_t e = first;
+    for (; e + stride < e1; e += 2 * stride) {
+        const int32_t x0 = __ldg(&col[e]);
+        const int32_t x1 = __ldg(&col[e + stride]);
+        const uint8_t f0 = __ldg(&flc[x0]);
+        const uint8_t f1 = __ldg(&flc[x1]);
+        if (f0) or_row<W>(a, Fc, x0);
+        if (f1) or_row<W>(a, Fc, x1);
+    }
+    if (e < e1) {
+        const int32_t x0 = __ldg(&col[e]);
+        if (__ldg(&flc[x0])) or_row<W>(a, Fc, x0);
+    }
+}
+
+// OR a across the G lanes of each aligned lane group (G a power of two <= 32).
+template <int W, int G>
+__device__ __forceinline__ void group_or(uint64_t (&a)[W])
+{
+#pragma unroll
+    for (int off = 1; off < G; off <<= 1) {
+#pragma unroll
+        for (int k = 0; k < W; k++) a[k] |= __shfl_xor_sync(kFull, a[k], off);
+    }
+}
+
+// a[i] without dynamic register indexing.
+template <int W>
+__device__ __forceinline__ uint64_t select_word(const uint64_t (&a)[W], int i)
+{
+    uint64_t r = 0;
+#pragma unroll
+    for (int k = 0; k < W; k++)
+        if (k == i) r = a[k];
+    return r;
+}
+
 // ---------------------------------------------------------------------------
 // level 0: sources. One block of up to 1024 threads; resets the level ring.
 // ---------------------------------------------------------------------------
@@ -195,6 +258,73 @@ __global__ void k_seed(const int32_t *__restrict__ src, int32_t ns, BfsBufs b, c
         b.ctl->t = ns;
         b.ctl->fe[0] = s_fe;
         if (s_fe) atomicAdd(b.edges, s_fe);  // every source scans its own row
+    }
+}
+
+
+// Non-last levels: store the new words of vertex y (lanes gi < W of its
+// group hold word gi), mark it in the next frontier, append it to Q (and T
+// on its first visit). Whole warp calls.
+template <int W, int G>
+__device__ __forceinline__ void finish_vertex(bool act, int32_t y, int32_t dy, uint64_t nw, uint64_t v, int gi,
+                                              int grp, uint64_t *__restrict__ V, uint64_t *__restrict__ Fn,
+                                              uint8_t *__restrict__ fln, const BfsBufs &b, int nslot, Acc &acc)
+{
+    const unsigned gmask = (G == 32) ? kFull : ((1u << G) - 1u);
+    const unsigned any = __ballot_sync(kFull, nw != 0);
+    const unsigned vany = __ballot_sync(kFull, v != 0);
+    const bool gany = ((any >> (grp * G)) & gmask) != 0;
+    const bool gv = ((vany >> (grp * G)) & gmask) != 0;
+    if (act && gany && gi < W) {
+        Fn[(size_t)y * W + gi] = nw;
+        if (nw) V[(size_t)y * W + gi] = v | nw;
+        acc.scanned += (unsigned long long)__popcll(nw) * (unsigned long long)dy;
+    }
+    const bool lead = act && gany && gi == 0;
+    if (lead) fln[y] = 1;
+    append_frontier(lead, y, dy, b, nslot, acc);
+    warp_append(lead && !gv, y, b.T, &b.ctl->t);
+}
+
+// Pull over a vertex list with G lanes per vertex (32/G vertices per warp).
+template <int W, int G, bool LAST>
+__device__ __forceinline__ void pull_groups(const int32_t *__restrict__ list, int32_t count, int64_t warp,
+                                            int64_t nwarps, const GraphView &g, const uint32_t *__restrict__ alive,
+                                            uint64_t *__restrict__ V, const uint64_t *__restrict__ Fc,
+                                            const uint8_t *__restrict__ flc, uint64_t *__restrict__ Fn,
+                                            uint8_t *__restrict__ fln, const BfsBufs &b, int nslot, Swar &sw,
+                                            int32_t *cnt_s, Acc &acc)
+{
+    static_assert(G >= W && 32 % G == 0, "group");
+    constexpr int VPW = 32 / G;
+    const int lane = threadIdx.x & 31;
+    const int gi = lane % G;
+    const int grp = lane / G;
+    const int32_t *__restrict__ rp = g.row_ptr;
+    for (int64_t base = warp * VPW; base < count; base += nwarps * VPW) {  // warp-uniform
+        const int64_t idx = base + grp;
+        int32_t y = -1, dy = 0;
+        bool act = false;
+        uint64_t a[W];
+#pragma unroll
+        for (int k = 0; k < W; k++) a[k] = 0;
+        if (idx < count) {
+            y = list[idx];
+            if (is_alive(alive, y)) {
+                act = true;
+                const int32_t e0 = rp[y], e1 = rp[y + 1];
+                dy = e1 - e0;
+                gather_edges<W>(a, g.col, flc, Fc, e0 + gi, e1, G);
+            }
+        }
+        group_or<W, G>(a);
+        uint64_t nw = 0, v = 0;
+        if (act && gi < W) {
+            v = V[(size_t)y * W + gi];
+            nw = select_word<W>(a, gi) & ~v;
+        }
+        swar_step<W>(sw, nw, cnt_s);
+        if (!LAST) finish_vertex<W, G>(act, y, dy, nw, v, gi, grp, V, Fn, fln, b, nslot, acc);
     }
 }
 
@@ -288,93 +418,18 @@ __global__ void __launch_bounds__(kBlock) k_level(GraphView g, const uint32_t *_
         }
     } else {
         // ---------------- pull: every alive vertex gathers its neighbours ----
-        // finish one vertex: given the OR of its frontier neighbours (lanes of
-        // the group hold the W words), emit the new words.
-        // light: W lanes per vertex, 32/W vertices per warp
+        // A group of G lanes takes one vertex; each lane walks its own share
+        // of the edges (two independent chains per lane), ORs whole frontier
+        // rows into a[0..W-1], and the group ORs the lanes together. Lane
+        // gi < W of the group then finishes word gi.
+        // light (deg <= kLightMax): G = max(8, W) lanes per vertex
+        pull_groups<W, (W > 8 ? W : 8), LAST>(g.light, g.n_light, warp, nwarps, g, alive, V, Fc, flc, Fn, fln,
+                                              b, nslot, sw, cnt_s, acc);
+        // medium (deg <= kMediumMax): one warp per vertex
+        pull_groups<W, 32, LAST>(g.medium, g.n_medium, warp, nwarps, g, alive, V, Fc, flc, Fn, fln, b, nslot,
+                                 sw, cnt_s, acc);
+        // heavy: one block per vertex
         {
-            constexpr int VPW = 32 / W;
-            const int grp = lane / W;
-            const unsigned gmask = (W == 32) ? kFull : ((1u << W) - 1u);
-            for (int64_t base = warp * VPW; base < g.n_light; base += nwarps * VPW) {
-                const int64_t idx = base + grp;
-                uint64_t nw = 0, v = 0;
-                int32_t y = -1, dy = 0;
-                bool act = false;
-                if (idx < g.n_light) {
-                    y = g.light[idx];
-                    if (is_alive(alive, y)) {
-                        act = true;
-                        uint64_t a = 0;
-                        const int32_t e0 = rp[y], e1 = rp[y + 1];
-                        dy = e1 - e0;
-                        for (int32_t e = e0; e < e1; e++) {
-                            const int32_t x = __ldg(&col[e]);
-                            if (flc[x]) a |= Fc[(size_t)x * W + j];
-                        }
-                        v = V[(size_t)y * W + j];
-                        nw = a & ~v;
-                    }
-                }
-                swar_step<W>(sw, nw, cnt_s);
-                if (!LAST) {
-                    const unsigned any = __ballot_sync(kFull, nw != 0);
-                    const unsigned vany = __ballot_sync(kFull, v != 0);
-                    const bool gany = ((any >> (grp * W)) & gmask) != 0;
-                    const bool gv = ((vany >> (grp * W)) & gmask) != 0;
-                    if (act && gany) {
-                        Fn[(size_t)y * W + j] = nw;
-                        if (nw) V[(size_t)y * W + j] = v | nw;
-                        acc.scanned += (unsigned long long)__popcll(nw) * (unsigned long long)dy;
-                    }
-                    const bool lead = act && gany && j == 0;
-                    if (lead) fln[y] = 1;
-                    append_frontier(lead, y, dy, b, nslot, acc);
-                    warp_append(lead && !gv, y, b.T, &b.ctl->t);
-                }
-            }
-        }
-        // medium: one warp per vertex, 32/W neighbour slots
-        {
-            constexpr int SLOTS = 32 / W;
-            const int slot = lane / W;
-            for (int64_t i = warp; i < g.n_medium; i += nwarps) {
-                const int32_t y = g.medium[i];
-                const bool act = is_alive(alive, y);  // warp-uniform
-                uint64_t nw = 0, v = 0;
-                const int32_t e0 = rp[y], e1 = rp[y + 1];
-                if (act) {
-                    uint64_t a = 0;
-                    for (int32_t e = e0 + slot; e < e1; e += SLOTS) {
-                        const int32_t x = __ldg(&col[e]);
-                        if (flc[x]) a |= Fc[(size_t)x * W + j];
-                    }
-#pragma unroll
-                    for (int off = W; off < 32; off <<= 1) a |= __shfl_xor_sync(kFull, a, off);
-                    if (lane < W) {
-                        v = V[(size_t)y * W + j];
-                        nw = a & ~v;
-                    }
-                }
-                swar_step<W>(sw, nw, cnt_s);
-                if (!LAST) {
-                    const bool gany = __ballot_sync(kFull, nw != 0) != 0;
-                    const bool gv = __ballot_sync(kFull, v != 0) != 0;
-                    if (act && gany && lane < W) {
-                        Fn[(size_t)y * W + j] = nw;
-                        if (nw) V[(size_t)y * W + j] = v | nw;
-                        acc.scanned += (unsigned long long)__popcll(nw) * (unsigned long long)(e1 - e0);
-                    }
-                    const bool lead = act && gany && lane == 0;
-                    if (lead) fln[y] = 1;
-                    append_frontier(lead, y, e1 - e0, b, nslot, acc);
-                    warp_append(lead && !gv, y, b.T, &b.ctl->t);
-                }
-            }
-        }
-        // heavy: one block per vertex, kBlock/W neighbour slots
-        {
-            const int slot = threadIdx.x / W;
-            const int slots = blockDim.x / W;
             const int wid = threadIdx.x >> 5;
             const int nwarp_blk = blockDim.x >> 5;
             for (int64_t i = blockIdx.x; i < g.n_heavy; i += gridDim.x) {
@@ -382,38 +437,24 @@ __global__ void __launch_bounds__(kBlock) k_level(GraphView g, const uint32_t *_
                 const bool act = is_alive(alive, y);  // block-uniform
                 const int32_t e0 = rp[y], e1 = rp[y + 1];
                 if (act) {
-                    uint64_t a = 0;
-                    for (int32_t e = e0 + slot; e < e1; e += slots) {
-                        const int32_t x = __ldg(&col[e]);
-                        if (flc[x]) a |= Fc[(size_t)x * W + j];
-                    }
+                    uint64_t a[W];
 #pragma unroll
-                    for (int off = W; off < 32; off <<= 1) a |= __shfl_xor_sync(kFull, a, off);
-                    if (lane < W) red[wid][lane] = a;
+                    for (int k = 0; k < W; k++) a[k] = 0;
+                    gather_edges<W>(a, col, flc, Fc, e0 + (int32_t)threadIdx.x, e1, (int32_t)blockDim.x);
+                    group_or<W, 32>(a);
+                    if (lane < W) red[wid][lane] = select_word<W>(a, lane);
                 }
                 __syncthreads();
                 if (wid == 0) {
                     uint64_t nw = 0, v = 0;
                     if (act && lane < W) {
-                        uint64_t a = 0;
-                        for (int w = 0; w < nwarp_blk; w++) a |= red[w][lane];
+                        uint64_t m = 0;
+                        for (int w = 0; w < nwarp_blk; w++) m |= red[w][lane];
                         v = V[(size_t)y * W + j];
-                        nw = a & ~v;
+                        nw = m & ~v;
                     }
                     swar_step<W>(sw, nw, cnt_s);
-                    if (!LAST) {
-                        const bool gany = __ballot_sync(kFull, nw != 0) != 0;
-                        const bool gv = __ballot_sync(kFull, v != 0) != 0;
-                        if (act && gany && lane < W) {
-                            Fn[(size_t)y * W + j] = nw;
-                            if (nw) V[(size_t)y * W + j] = v | nw;
-                            acc.scanned += (unsigned long long)__popcll(nw) * (unsigned long long)(e1 - e0);
-                        }
-                        const bool lead = act && gany && lane == 0;
-                        if (lead) fln[y] = 1;
-                        append_frontier(lead, y, e1 - e0, b, nslot, acc);
-                        warp_append(lead && !gv, y, b.T, &b.ctl->t);
-                    }
+                    if (!LAST) finish_vertex<W, 32>(act, y, e1 - e0, nw, v, lane, 0, V, Fn, fln, b, nslot, acc);
                 }
                 __syncthreads();
             }

@@ -84,15 +84,29 @@ struct LevelTimer {
 
 // Round state of the peeler, device-resident.
 struct PeelState {
-    int32_t k;        // current level (never decreases)
-    int32_t min_deg;  // scratch for the min-reduction (INT32_MAX between uses)
     int32_t nD;       // vertices deleted this round
-    int32_t nA;       // affected vertices this round
+    int32_t nA;       // affected vertices this round (all classes)
     int32_t alive;    // vertices still alive
     int32_t round;    // current round
     int32_t err;      // device-side consistency error code (0 = none)
-    int32_t pad;
+    int32_t aq[3];    // affected-BFS frontier list lengths (ring of three)
     unsigned long long m_alive;  // CSR entries of alive vertices
+};
+
+// Per-graph peel parameters. One context may hold several disjoint graphs
+// (a batch); each peels with its own level k_g and hop bound h_g. Graphs
+// with equal h form an h-class; the sources of a class are recomputed in
+// BFS batches of that h.
+struct PeelView {
+    int32_t G;               // graphs
+    int32_t ncls;            // h-classes
+    const int32_t *gid;      // [n] graph of each vertex, or nullptr when G == 1
+    int32_t *kg;             // [G] current level of each graph
+    int32_t *ming;           // [G] min scratch (INT32_MAX between rounds)
+    const int32_t *hg;       // [G] h of each graph
+    const int32_t *cls;      // [G] h-class of each graph
+    const int32_t *cls_off;  // [ncls] start of each class's region of the source list
+    int32_t *nAc;            // [ncls] affected vertices per class this round
 };
 
 // ---- launchers (khcore_kernels.cu) -----------------------------------------
@@ -110,18 +124,24 @@ cudaError_t run_bfs_batch(int W, const GraphView &g, const uint32_t *alive, cons
                           const int32_t *src, int32_t ns, int32_t h, int32_t *deg, BfsTuning tune,
                           int grid, cudaStream_t s, int64_t *launches, LevelTimer *timer);
 
-// Peel round pieces.
-cudaError_t launch_min_alive_deg(const GraphView &g, const uint32_t *alive, const int32_t *deg,
-                                 PeelState *st, int grid, cudaStream_t s);
-cudaError_t launch_set_level(PeelState *st, cudaStream_t s);
-// Also subtracts the CSR degree of every deleted vertex from st->m_alive.
-cudaError_t launch_peel_compact(const GraphView &g, uint32_t *alive, const int32_t *deg,
-                                PeelState *st, int32_t *core, int32_t *rnd, uint32_t *fr0,
-                                int grid, cudaStream_t s);
-cudaError_t launch_affected_level(const GraphView &g, const uint32_t *alive, const uint32_t *fr_cur,
-                                  uint32_t *fr_next, uint32_t *vis, int grid, cudaStream_t s);
-cudaError_t launch_compact_affected(const GraphView &g, const uint32_t *alive, const uint32_t *vis,
-                                    PeelState *st, int32_t *list, int grid, cudaStream_t s);
+// Peel round pieces (khcore_peel.cu).
+cudaError_t launch_min_alive_deg(const GraphView &g, const uint32_t *alive, const int32_t *deg, const PeelView &p,
+                                 int grid, cudaStream_t s);
+cudaError_t launch_set_level(const PeelView &p, PeelState *st, cudaStream_t s);
+// Also subtracts the CSR degree of every deleted vertex from st->m_alive,
+// sets the deleted vertices' bits in vis and appends them to dlist (st->aq[0]).
+cudaError_t launch_peel_compact(const GraphView &g, uint32_t *alive, const int32_t *deg, const PeelView &p,
+                                PeelState *st, int32_t *core, int32_t *rnd, uint32_t *vis, int32_t *dlist, int grid,
+                                cudaStream_t s);
+// Affected-set BFS, push direction. aq[3] are frontier lists (ring of three;
+// slot 0 holds D after launch_peel_compact); vis is the visited bitset (D's
+// bits set by the compaction); every newly reached alive vertex is appended
+// to the next frontier and to its class region of A (p.nAc).
+cudaError_t launch_affected_level(const GraphView &g, const uint32_t *alive, int lvl, int32_t *const aq[3],
+                                  uint32_t *vis, const PeelView &p, PeelState *st, int32_t *A, int last, int grid,
+                                  cudaStream_t s);
+// st->nA = sum of p.nAc.
+cudaError_t launch_sum_classes(const PeelView &p, PeelState *st, cudaStream_t s);
 
 int max_blocks_per_sm_bfs(int W);
 

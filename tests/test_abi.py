@@ -83,3 +83,15 @@ def test_malformed_csr_is_einval(lib, case):
 def test_compiled_for_sm_103a_only():
     from paper_2006_03372_gb300 import _build
     assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_batch_create_rejects_bad_graph(lib):
+    import paper_2006_03372_gb300 as kh
+    good, bad = gg.cycle(5), gg.cycle(6)
+    col = bad.col.copy()
+    col[0] = 0  # self-loop in graph 1
+    bad = gg.Graph(bad.n, bad.row_ptr, col)
+    v_off, e_off, rp, cl = kh.pack_graphs([good, bad])
+    with pytest.raises(kh.KHCoreError) as ei:
+        kh.khcore_batch_create(v_off, e_off, rp, cl)
+    assert ei.value.status == 1 and "graph 1" in str(ei.value)

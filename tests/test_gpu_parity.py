@@ -151,3 +151,39 @@ def test_repeatable_and_order_independent(kh):
     assert (c1 == c2).all()
     assert (c3[perm] == c1).all()
     assert (c1 == oracle.peel(g, 3)).all()
+
+
+def test_batch_matches_solo_oracle(kh):
+    """Many graphs of uneven size in one context, each with its own h: every
+    graph's core indices equal the oracle's on that graph alone."""
+    rng = gg.Stream(77, "batch-test")
+    graphs, hs = [], []
+    for i in range(24):
+        n = int(5 + rng.below(200, 1)[0])
+        if i % 3 == 0:
+            graphs.append(gg.erdos_renyi_gnm(n, min(3 * n, n * (n - 1) // 2), 500 + i))
+        elif i % 3 == 1:
+            graphs.append(gg.chung_lu(n, min(4.0, n / 4), 2.3, max(n / 2, 8.0), 600 + i))
+        else:
+            graphs.append(gg.cycle(n))
+        hs.append(int(1 + rng.below(4, 1)[0]))
+    graphs.append(gg.empty(3))
+    hs.append(2)
+    v_off, e_off, rp, col = kh.pack_graphs(graphs)
+    ctx = kh.khcore_batch_create(v_off, e_off, rp, col)
+    try:
+        for w in [1, 4, 16]:
+            kh.khcore_set_words(ctx, w)
+            core, rnd, st = kh.khcore_batch_decompose(ctx, np.array(hs, dtype=np.int32))
+            for g, h, a, b in zip(graphs, hs, v_off[:-1], v_off[1:]):
+                assert (core[a:b] == oracle.peel(g, h)).all(), (g.name, h, w)
+                assert oracle.certificate(g, h, core[a:b], rnd[a:b])[0] == 0
+        # one h for the whole batch through the single-h entry point
+        core = kh.khcore_decompose(ctx, 2)
+        for g, a, b in zip(graphs, v_off[:-1], v_off[1:]):
+            assert (core[a:b] == oracle.peel(g, 2)).all()
+        d = kh.khcore_hdegrees(ctx, 3)
+        for g, a, b in zip(graphs, v_off[:-1], v_off[1:]):
+            assert (d[a:b] == oracle.hdegrees(g, 3)).all()
+    finally:
+        kh.khcore_destroy(ctx)
