@@ -78,6 +78,9 @@ typedef struct {
     double level_bytes;        /* their summed algorithmic bytes: per launch
                                   4*n_b + 4*m_b + 16*W*n_b for the n_b alive
                                   rows and m_b CSR entries it scans */
+    int64_t recomputed_total;  /* affected vertices whose h-degree was recomputed
+                                  by BFS (those closer than h to the deleted set);
+                                  the others were updated by counting */
 } khcore_stats;
 
 /*
@@ -107,6 +110,17 @@ khcore_status khcore_create(int32_t n, const int32_t *row_ptr, const int32_t *co
  * Computed by a multi-source h-bounded BFS on 64-bit source bitsets.
  */
 khcore_status khcore_hdegrees(khcore_ctx *ctx, int32_t h, int32_t *deg_out);
+
+/*
+ * khcore_hdegrees_of — d_v^h(G) for the listed vertices only (a subset of
+ * the sources of khcore_hdegrees; same BFS, fewer batches).
+ *   count    number of listed vertices, 0 <= count <= n
+ *   verts    int32[count] distinct vertex ids (host or device); EINVAL on a
+ *            repeated or out-of-range id
+ *   deg_out  int32[count] (host or device); deg_out[i] = d^h of verts[i]
+ */
+khcore_status khcore_hdegrees_of(khcore_ctx *ctx, int32_t h, int32_t count, const int32_t *verts,
+                                 int32_t *deg_out);
 
 /*
  * khcore_decompose — core_h(v) for every vertex (problem statement, Sec. II).
@@ -190,6 +204,57 @@ khcore_status khcore_set_push_alpha(khcore_ctx *ctx, int32_t alpha);
  * their count, summed time and algorithmic bytes. Results do not change.
  */
 khcore_status khcore_set_profiling(khcore_ctx *ctx, int32_t on);
+
+/* ---------------------------------------------------------------------------
+ * Serving: a request server with continuous batching.
+ *
+ * Requests wait in arrival order. Each of `slots` worker threads owns a CUDA
+ * stream on the device current at khcore_server_create; a free worker admits
+ * every queued request that still fits the device-memory budget (at most
+ * max_batch), decomposes them together as one batch context
+ * (khcore_batch_create / khcore_batch_decompose) and publishes the results.
+ * Workers run concurrently, so requests that arrive while others are on the
+ * GPU are admitted as slots and budget free up, and their work overlaps on the
+ * device. A request's core indices equal those of a solo khcore_decompose.
+ * ------------------------------------------------------------------------- */
+typedef struct khcore_server khcore_server;
+
+/* Device bytes a request with n vertices and m CSR entries is charged
+ * against the budget: CSR, per-vertex state and frontier lists, and BFS
+ * bitsets for the largest W (16). */
+size_t khcore_request_bytes(int32_t n, int64_t m);
+
+/* budget: device bytes all admitted requests may use at once (> 0);
+ * slots: worker threads / streams (1..64); max_batch: requests per batch
+ * (>= 1). EINVAL on bad arguments, ECUDA without a device. */
+khcore_status khcore_server_create(size_t device_bytes_budget, int32_t slots, int32_t max_batch,
+                                   khcore_server **out);
+
+/* Queue one decomposition. The graph (int32 CSR, host memory, both edge
+ * directions, as for khcore_create but not validated) is copied, so the
+ * caller may free it on return. ticket receives the request id. ENOMEM if
+ * the request alone exceeds the budget (it could never be admitted). */
+khcore_status khcore_server_submit(khcore_server *srv, int32_t n, const int32_t *row_ptr,
+                                   const int32_t *col, int32_t h, uint64_t *ticket);
+
+/* done = 1 once the request has finished (EINVAL for an unknown ticket). */
+khcore_status khcore_server_poll(khcore_server *srv, uint64_t ticket, int32_t *done);
+
+/* Wait at most timeout_s seconds (ETIMEOUT after that; the request stays
+ * queryable) for the request, copy its core indices to core_out (int32[n],
+ * host; may be NULL) and its latency (finish minus submit, ms) to
+ * latency_ms (may be NULL), and forget the ticket. Returns the request's own
+ * status. */
+khcore_status khcore_server_wait(khcore_server *srv, uint64_t ticket, int32_t *core_out,
+                                 double timeout_s, double *latency_ms);
+
+/* Counters: requests queued, requests completed, batches run, budget bytes
+ * in use (each pointer may be NULL). */
+khcore_status khcore_server_stats(khcore_server *srv, int64_t *queued, int64_t *completed,
+                                  int64_t *batches, size_t *bytes_in_use);
+
+/* Stop the workers after their current batch; queued requests are dropped. */
+void khcore_server_destroy(khcore_server *srv);
 
 /* Release every device and host resource of the context. NULL is a no-op. */
 void khcore_destroy(khcore_ctx *ctx);

@@ -31,6 +31,7 @@ __all__ = [
     "khcore_set_push_alpha",
     "khcore_status_string", "Stats",
     "KHCore", "library_path", "load_library", "khcore_batch_create", "khcore_batch_decompose", "pack_graphs",
+    "khcore_hdegrees_of", "Server", "request_bytes",
 ]
 
 STATUS = {0: "KHCORE_OK", 1: "KHCORE_EINVAL", 2: "KHCORE_ENOMEM", 3: "KHCORE_ECUDA",
@@ -50,7 +51,8 @@ class Stats(ctypes.Structure):
                 ("affected_total", ctypes.c_int64), ("source_batches", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("device_ms", ctypes.c_double),
                 ("edges_traversed", ctypes.c_int64), ("level_launches", ctypes.c_int64),
-                ("level_ms", ctypes.c_double), ("level_bytes", ctypes.c_double)]
+                ("level_ms", ctypes.c_double), ("level_bytes", ctypes.c_double),
+                ("recomputed_total", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -102,6 +104,24 @@ def load_library(build_if_missing: bool = False):
         lib.khcore_num_vertices.restype = i32
         lib.khcore_num_entries.argtypes = [P]
         lib.khcore_num_entries.restype = i64
+        lib.khcore_hdegrees_of.argtypes = [P, i32, i32, P, P]
+        lib.khcore_hdegrees_of.restype = ctypes.c_int
+        sz = ctypes.c_size_t
+        lib.khcore_request_bytes.argtypes = [i32, i64]
+        lib.khcore_request_bytes.restype = sz
+        lib.khcore_server_create.argtypes = [sz, i32, i32, ctypes.POINTER(P)]
+        lib.khcore_server_create.restype = ctypes.c_int
+        lib.khcore_server_submit.argtypes = [P, i32, P, P, i32, ctypes.POINTER(ctypes.c_uint64)]
+        lib.khcore_server_submit.restype = ctypes.c_int
+        lib.khcore_server_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(i32)]
+        lib.khcore_server_poll.restype = ctypes.c_int
+        lib.khcore_server_wait.argtypes = [P, ctypes.c_uint64, P, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+        lib.khcore_server_wait.restype = ctypes.c_int
+        lib.khcore_server_stats.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                            ctypes.POINTER(sz)]
+        lib.khcore_server_stats.restype = ctypes.c_int
+        lib.khcore_server_destroy.argtypes = [P]
+        lib.khcore_server_destroy.restype = None
         lib.khcore_num_graphs.argtypes = [P]
         lib.khcore_num_graphs.restype = i32
         lib.khcore_batch_create.argtypes = [i32, P, P, P, P, u32, P, ctypes.POINTER(P)]
@@ -209,6 +229,18 @@ def khcore_hdegrees(ctx, h: int, deg_out=None):
     return out
 
 
+def khcore_hdegrees_of(ctx, h: int, verts, deg_out=None):
+    """d_v^h(G) for the listed (distinct) vertices."""
+    lib = load_library()
+    pv, k = _ptr(verts)
+    count = len(verts)
+    out = np.empty(count, dtype=np.int32) if deg_out is None else deg_out
+    po, _ = _ptr(out)
+    _check(lib, ctx, lib.khcore_hdegrees_of(ctx, int(h), int(count), pv, po))
+    del k
+    return out
+
+
 def khcore_decompose(ctx, h: int, core_out=None):
     """core_h(v) for all v."""
     lib = load_library()
@@ -272,6 +304,71 @@ def pack_graphs(graphs):
     rp = np.concatenate([np.asarray(g.row_ptr, dtype=np.int32) for g in graphs]) if graphs else np.zeros(0, np.int32)
     col = np.concatenate([np.asarray(g.col, dtype=np.int32) for g in graphs]) if graphs else np.zeros(0, np.int32)
     return v_off, e_off, rp, col
+
+
+class Server:
+    """Request server with continuous batching (khcore_server_* in the C ABI)."""
+
+    def __init__(self, budget_bytes: int, slots: int = 2, max_batch: int = 256):
+        self.lib = load_library()
+        self.h = ctypes.c_void_p()
+        st = self.lib.khcore_server_create(int(budget_bytes), int(slots), int(max_batch), ctypes.byref(self.h))
+        if st != 0:
+            raise KHCoreError(st, "khcore_server_create failed")
+        self._n = {}
+
+    def submit(self, n, row_ptr, col, h) -> int:
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        cl = np.ascontiguousarray(col, dtype=np.int32)
+        t = ctypes.c_uint64()
+        st = self.lib.khcore_server_submit(self.h, int(n), rp.ctypes.data_as(ctypes.c_void_p),
+                                           cl.ctypes.data_as(ctypes.c_void_p) if cl.size else None, int(h),
+                                           ctypes.byref(t))
+        if st != 0:
+            raise KHCoreError(st, "khcore_server_submit failed")
+        self._n[t.value] = int(n)
+        return t.value
+
+    def done(self, ticket) -> bool:
+        d = ctypes.c_int32()
+        st = self.lib.khcore_server_poll(self.h, ctypes.c_uint64(ticket), ctypes.byref(d))
+        if st != 0:
+            raise KHCoreError(st, "khcore_server_poll failed")
+        return bool(d.value)
+
+    def wait(self, ticket, timeout_s: float = 600.0):
+        """(core, latency_ms) of a request."""
+        n = self._n.pop(ticket)
+        out = np.empty(max(n, 1), dtype=np.int32)
+        lat = ctypes.c_double()
+        st = self.lib.khcore_server_wait(self.h, ctypes.c_uint64(ticket), out.ctypes.data_as(ctypes.c_void_p),
+                                         float(timeout_s), ctypes.byref(lat))
+        if st != 0:
+            if st == 4:
+                self._n[ticket] = n
+            raise KHCoreError(st, "khcore_server_wait failed")
+        return out[:n], lat.value
+
+    def stats(self):
+        q, c, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        u = ctypes.c_size_t()
+        self.lib.khcore_server_stats(self.h, ctypes.byref(q), ctypes.byref(c), ctypes.byref(b), ctypes.byref(u))
+        return dict(queued=q.value, completed=c.value, batches=b.value, bytes_in_use=u.value)
+
+    def close(self):
+        if self.h:
+            self.lib.khcore_server_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def request_bytes(n: int, m: int) -> int:
+    return int(load_library().khcore_request_bytes(int(n), int(m)))
 
 
 class KHCore:

@@ -38,7 +38,10 @@ struct khcore_ctx {
     // per-graph peel parameters (device)
     int32_t *kg = nullptr, *ming = nullptr, *hg = nullptr, *gcls = nullptr;
     int32_t *cls_off = nullptr, *nAc = nullptr;  // [G] capacity each (ncls <= G)
+    int32_t *nDc = nullptr, *inner = nullptr, *clsh = nullptr;  // [G] capacity each
     int32_t *cls_src = nullptr;                  // [n] vertices grouped by h-class
+    int32_t *dcls = nullptr;                     // [n] deleted vertices grouped by h-class (per round)
+    int32_t *dcount = nullptr;                   // [n] deleted vertices within h (outer-shell update)
 
     // peel state (device)
     uint32_t *alive = nullptr;
@@ -46,7 +49,7 @@ struct khcore_ctx {
     uint32_t *vis = nullptr;
     PeelState *st = nullptr;
     PeelState *st_host = nullptr;  // pinned mirror
-    int32_t *nAc_host = nullptr;   // pinned mirror of nAc
+    int32_t *nAc_host = nullptr;   // pinned mirror of nAc, inner, nDc (3 x G)
 
     // BFS buffers, sized for W_alloc words per vertex
     int W_req = 0;  // 0 = automatic
@@ -259,7 +262,7 @@ khcore_status flush_timer(khcore_ctx *c)
 // n_b / m_b: alive rows and their CSR entries (direction choice and
 // algorithmic bytes).
 khcore_status hdeg_sources(khcore_ctx *c, int W, int32_t h, const int32_t *src, int32_t ns, int64_t n_b,
-                           int64_t m_b, khcore_stats *stt)
+                           int64_t m_b, khcore_stats *stt, int32_t *rowcnt = nullptr)
 {
     const GraphView g = c->view();
     BfsBufs b;
@@ -276,6 +279,7 @@ khcore_status hdeg_sources(khcore_ctx *c, int W, int32_t h, const int32_t *src, 
     b.ctl = c->ctl;
     b.cnt = c->cnt;
     b.edges = c->edges;
+    b.rowcnt = rowcnt;
     BfsTuning tune;
     tune.alpha = c->push_alpha;
     tune.m_alive = (unsigned long long)m_b;
@@ -385,10 +389,16 @@ khcore_status setup_ctx(khcore_ctx *c, const std::vector<int32_t> &rp, const std
     A(dev_alloc(&c->gcls, (size_t)c->G));
     A(dev_alloc(&c->cls_off, (size_t)c->G));
     A(dev_alloc(&c->nAc, (size_t)c->G));
+    A(dev_alloc(&c->nDc, (size_t)c->G));
+    A(dev_alloc(&c->inner, (size_t)c->G));
+    A(dev_alloc(&c->clsh, (size_t)c->G));
+    A(dev_alloc(&c->dcls, (size_t)n));
+    A(dev_alloc(&c->dcount, (size_t)n));
     if (c->G > 1) A(dev_alloc(&c->gid, (size_t)n));
     if (st != KHCORE_OK) return st;
     e = cudaMallocHost((void **)&c->st_host, sizeof(PeelState));
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->nAc_host, sizeof(int32_t) * (size_t)c->G);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->nAc_host, 3 * sizeof(int32_t) * (size_t)c->G);
+    if (e == cudaSuccess && n) e = cudaMemsetAsync(c->dcount, 0, sizeof(int32_t) * (size_t)n, c->stream);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
     if (e == cudaSuccess)
@@ -469,6 +479,7 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
     pv.cls = c->gcls;
     pv.cls_off = c->cls_off;
     pv.nAc = c->nAc;
+    pv.nDc = c->nDc;
 
     CU(cudaEventRecord(c->ev0, c->stream));
     PeelState init;
@@ -486,6 +497,8 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
     CU(cudaMemcpyAsync(c->hg, hg.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemcpyAsync(c->gcls, gcls.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemcpyAsync(c->cls_off, cls_off.data(), sizeof(int32_t) * ncls, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->clsh, cls_h.data(), sizeof(int32_t) * ncls, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemsetAsync(c->inner, 0, sizeof(int32_t) * ncls, c->stream));
     CU(cudaMemcpyAsync(c->cls_src, cls_src.data(), sizeof(int32_t) * c->n, cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemsetAsync(c->edges, 0, sizeof(unsigned long long), c->stream));
     CU(launch_alive_init(c->alive, c->n, c->stream));
@@ -509,17 +522,21 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         CU(launch_min_alive_deg(g, c->alive, c->deg, pv, grid, c->stream));
         CU(launch_set_level(pv, c->st, c->stream));
         CU(cudaMemsetAsync(c->vis, 0, nwb, c->stream));
-        CU(launch_peel_compact(g, c->alive, c->deg, pv, c->st, c->core, c->rnd, c->vis, c->Q[0], grid, c->stream));
+        CU(launch_peel_compact(g, c->alive, c->deg, pv, c->st, c->core, c->rnd, c->vis, c->Q[0], c->dcls, grid,
+                               c->stream));
         stt.kernel_launches += 3;
         for (int lvl = 0; lvl < hmax; lvl++) {
+            CU(launch_snapshot_inner(pv, c->clsh, lvl, c->inner, c->stream));
             CU(launch_affected_level(g, c->alive, lvl, c->Q, c->vis, pv, c->st, c->src, lvl == hmax - 1, grid,
                                      c->stream));
-            stt.kernel_launches++;
+            stt.kernel_launches += 2;
         }
         CU(launch_sum_classes(pv, c->st, c->stream));
         stt.kernel_launches++;
         CU(cudaMemcpyAsync(c->st_host, c->st, sizeof(PeelState), cudaMemcpyDeviceToHost, c->stream));
         CU(cudaMemcpyAsync(c->nAc_host, c->nAc, sizeof(int32_t) * ncls, cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaMemcpyAsync(c->nAc_host + G, c->inner, sizeof(int32_t) * ncls, cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaMemcpyAsync(c->nAc_host + 2 * G, c->nDc, sizeof(int32_t) * ncls, cudaMemcpyDeviceToHost, c->stream));
         CU(cudaStreamSynchronize(c->stream));
         const PeelState ps = *c->st_host;
         if (ps.nD <= 0)
@@ -536,11 +553,28 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         }
         round++;
         if (ps.alive == 0) break;
+        // Affected vertices closer than h to D get their h-degree recomputed;
+        // those exactly h away lose exactly the deleted vertices within h
+        // (Observation 2 with s = h), counted by a BFS from D (row counts),
+        // or 1 when a single vertex went.
         for (int32_t k = 0; k < ncls; k++) {
             const int32_t na = c->nAc_host[k];
-            if (na > 0 && (s = hdeg_sources(c, W, cls_h[k], c->src + cls_off[k], na, ps.alive, (int64_t)ps.m_alive,
+            const int32_t ni = std::min(c->nAc_host[G + k], na);
+            const int32_t nd = c->nAc_host[2 * G + k];
+            if (na == 0) continue;
+            if (ni > 0 && (s = hdeg_sources(c, W, cls_h[k], c->src + cls_off[k], ni, ps.alive, (int64_t)ps.m_alive,
                                             &stt)) != KHCORE_OK)
                 return s;
+            stt.recomputed_total += ni;
+            if (na > ni) {
+                const bool single = (ps.nD == 1);
+                if (!single &&
+                    (s = hdeg_sources(c, W, cls_h[k], c->dcls + cls_off[k], nd, ps.alive, (int64_t)ps.m_alive, &stt,
+                                      c->dcount)) != KHCORE_OK)
+                    return s;
+                CU(launch_apply_dcount(c->src + cls_off[k], ni, na, single ? nullptr : c->dcount, c->deg, c->stream));
+                stt.kernel_launches++;
+            }
         }
         // advance the device-side round counter
         c->st_host->round = round;
@@ -617,6 +651,7 @@ void khcore_destroy(khcore_ctx *c)
     cudaSetDevice(c->device);
     if (c->stream && !c->failed) cudaStreamSynchronize(c->stream);
     void *bufs[] = {c->row_ptr, c->col, c->classes, c->gid, c->kg, c->ming, c->hg, c->gcls, c->cls_off, c->nAc,
+                    c->nDc, c->inner, c->clsh, c->dcls, c->dcount,
                     c->cls_src, c->alive, c->deg, c->core, c->rnd, c->src, c->vis, c->st, c->V, c->F[0], c->F[1],
                     c->flag[0], c->flag[1], c->Q[0], c->Q[1], c->Q[2], c->QH[0], c->QH[1], c->QH[2], c->T, c->ctl,
                     c->cnt, c->edges};
@@ -758,6 +793,44 @@ khcore_status khcore_hdegrees(khcore_ctx *c, int32_t h, int32_t *deg_out)
     if ((s = hdeg_sources(c, W, hmax, c->src, c->n, c->n, c->m, nullptr)) != KHCORE_OK) return s;
     if ((s = write_out(c, deg_out, c->deg)) != KHCORE_OK) return s;
     CU(cudaStreamSynchronize(c->stream));
+    return KHCORE_OK;
+}
+
+khcore_status khcore_hdegrees_of(khcore_ctx *c, int32_t h, int32_t count, const int32_t *verts, int32_t *deg_out)
+{
+    khcore_status s = check_ctx(c);
+    if (s != KHCORE_OK) return s;
+    if (h < 1) return fail(c, KHCORE_EINVAL, "h must be >= 1 (got %d)", h);
+    if (count < 0 || count > c->n) return fail(c, KHCORE_EINVAL, "count %d outside [0, %d]", count, c->n);
+    if (count == 0) return KHCORE_OK;
+    if (!verts || !deg_out) return fail(c, KHCORE_EINVAL, "verts or deg_out is NULL");
+    std::vector<int32_t> vs;
+    if (fetch(vs, verts, (size_t)count) != cudaSuccess) return fail(c, KHCORE_ECUDA, "cannot read verts");
+    {
+        std::vector<uint8_t> seen((size_t)c->n, 0);
+        for (int32_t i = 0; i < count; i++) {
+            if (vs[i] < 0 || vs[i] >= c->n) return fail(c, KHCORE_EINVAL, "vertex %d outside [0, %d)", vs[i], c->n);
+            if (seen[vs[i]]++) return fail(c, KHCORE_EINVAL, "vertex %d listed twice", vs[i]);
+        }
+    }
+    const int W = c->W_req ? c->W_req : auto_words(c->n);
+    if ((s = ensure_bfs(c, W)) != KHCORE_OK) return s;
+    int32_t hmax = 1;
+    for (int32_t g = 0; g < c->G; g++) hmax = std::max(hmax, effective_h(c->v_off[g + 1] - c->v_off[g], h));
+    CU(launch_alive_init(c->alive, c->n, c->stream));
+    CU(cudaMemcpyAsync(c->src, vs.data(), sizeof(int32_t) * (size_t)count, cudaMemcpyHostToDevice, c->stream));
+    if ((s = hdeg_sources(c, W, hmax, c->src, count, c->n, c->m, nullptr)) != KHCORE_OK) return s;
+    // gather deg[verts[i]] into deg_out[i] on the host side of the copy
+    std::vector<int32_t> all((size_t)c->n);
+    CU(cudaMemcpyAsync(all.data(), c->deg, sizeof(int32_t) * (size_t)c->n, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    std::vector<int32_t> outv((size_t)count);
+    for (int32_t i = 0; i < count; i++) outv[i] = all[vs[i]];
+    if (is_device_ptr(deg_out)) {
+        CU(cudaMemcpy(deg_out, outv.data(), sizeof(int32_t) * (size_t)count, cudaMemcpyHostToDevice));
+    } else {
+        std::memcpy(deg_out, outv.data(), sizeof(int32_t) * (size_t)count);
+    }
     return KHCORE_OK;
 }
 

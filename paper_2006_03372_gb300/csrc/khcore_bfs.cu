@@ -324,6 +324,12 @@ __device__ __forceinline__ void pull_groups(const int32_t *__restrict__ list, in
             nw = select_word<W>(a, gi) & ~v;
         }
         swar_step<W>(sw, nw, cnt_s);
+        if (b.rowcnt) {  // uniform
+            int32_t rc = __popcll(nw);
+#pragma unroll
+            for (int off = 1; off < G; off <<= 1) rc += __shfl_xor_sync(kFull, rc, off);
+            if (act && gi == 0 && rc) atomicAdd(&b.rowcnt[y], rc);
+        }
         if (!LAST) finish_vertex<W, G>(act, y, dy, nw, v, gi, grp, V, Fn, fln, b, nslot, acc);
     }
 }
@@ -386,6 +392,7 @@ __global__ void __launch_bounds__(kBlock) k_level(GraphView g, const uint32_t *_
                             atomicOr(reinterpret_cast<unsigned long long *>(&Fn[(size_t)y * W + j]),
                                      (unsigned long long)nbits);
                         fresh = nbits & ~(uint64_t)old;
+                        if (b.rowcnt && fresh) atomicAdd(&b.rowcnt[y], __popcll(fresh));
                     }
                 }
             }
@@ -454,6 +461,12 @@ __global__ void __launch_bounds__(kBlock) k_level(GraphView g, const uint32_t *_
                         nw = m & ~v;
                     }
                     swar_step<W>(sw, nw, cnt_s);
+                    if (b.rowcnt) {
+                        int32_t rc = __popcll(nw);
+#pragma unroll
+                        for (int off = 1; off < 32; off <<= 1) rc += __shfl_xor_sync(kFull, rc, off);
+                        if (act && lane == 0 && rc) atomicAdd(&b.rowcnt[y], rc);
+                    }
                     if (!LAST) finish_vertex<W, 32>(act, y, e1 - e0, nw, v, lane, 0, V, Fn, fln, b, nslot, acc);
                 }
                 __syncthreads();

@@ -56,6 +56,8 @@ constexpr int kPushChunk = 256;
 //            batches
 //   edges    plain-BFS-equivalent CSR entries scanned: sum over sources s and
 //            vertices x with dist(s, x) < h of deg(x) (for GTEPS reporting)
+//   rowcnt   optional [n]: when set, rowcnt[y] += number of batch sources
+//            that reach y at distance 1..h (row counts, the transpose of cnt)
 struct BfsBufs {
     uint64_t *V;
     uint64_t *F[2];
@@ -66,6 +68,7 @@ struct BfsBufs {
     LevelCtl *ctl;
     int32_t *cnt;
     unsigned long long *edges;
+    int32_t *rowcnt;
 };
 
 // Direction choice of one level: push when (sum of frontier degrees) * alpha
@@ -107,6 +110,7 @@ struct PeelView {
     const int32_t *cls;      // [G] h-class of each graph
     const int32_t *cls_off;  // [ncls] start of each class's region of the source list
     int32_t *nAc;            // [ncls] affected vertices per class this round
+    int32_t *nDc;            // [ncls] deleted vertices per class this round
 };
 
 // ---- launchers (khcore_kernels.cu) -----------------------------------------
@@ -129,9 +133,16 @@ cudaError_t launch_min_alive_deg(const GraphView &g, const uint32_t *alive, cons
                                  int grid, cudaStream_t s);
 cudaError_t launch_set_level(const PeelView &p, PeelState *st, cudaStream_t s);
 // Also subtracts the CSR degree of every deleted vertex from st->m_alive,
-// sets the deleted vertices' bits in vis and appends them to dlist (st->aq[0]).
+// sets the deleted vertices' bits in vis, appends them to dlist (st->aq[0])
+// and to their class region of dcls (p.nDc).
 cudaError_t launch_peel_compact(const GraphView &g, uint32_t *alive, const int32_t *deg, const PeelView &p,
-                                PeelState *st, int32_t *core, int32_t *rnd, uint32_t *vis, int32_t *dlist, int grid,
+                                PeelState *st, int32_t *core, int32_t *rnd, uint32_t *vis, int32_t *dlist,
+                                int32_t *dcls, int grid, cudaStream_t s);
+// Affected vertices list[0..total): those at index >= inner lie exactly h hops
+// from the deleted set, so (Observation 2) they lose exactly the deleted
+// vertices within h: deg[u] -= dcount[u] (or 1 when dcount is null). Resets
+// dcount[u] for every listed vertex.
+cudaError_t launch_apply_dcount(const int32_t *list, int32_t inner, int32_t total, int32_t *dcount, int32_t *deg,
                                 cudaStream_t s);
 // Affected-set BFS, push direction. aq[3] are frontier lists (ring of three;
 // slot 0 holds D after launch_peel_compact); vis is the visited bitset (D's
@@ -142,6 +153,9 @@ cudaError_t launch_affected_level(const GraphView &g, const uint32_t *alive, int
                                   cudaStream_t s);
 // st->nA = sum of p.nAc.
 cudaError_t launch_sum_classes(const PeelView &p, PeelState *st, cudaStream_t s);
+// Before affected-BFS level lvl: inner[c] = p.nAc[c] for every class whose
+// h is lvl + 1 (the vertices found so far are those closer than h).
+cudaError_t launch_snapshot_inner(const PeelView &p, const int32_t *cls_h, int lvl, int32_t *inner, cudaStream_t s);
 
 int max_blocks_per_sm_bfs(int W);
 

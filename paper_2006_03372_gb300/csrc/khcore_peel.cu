@@ -103,7 +103,10 @@ __global__ void k_set_level(PeelView p, PeelState *st)
         st->nA = 0;
         st->aq[0] = st->aq[1] = st->aq[2] = 0;
     }
-    for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < p.ncls; c += gridDim.x * blockDim.x) p.nAc[c] = 0;
+    for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < p.ncls; c += gridDim.x * blockDim.x) {
+        p.nAc[c] = 0;
+        p.nDc[c] = 0;
+    }
 }
 
 // D = {alive v : deg[v] <= k_g(v)}: core[v] = k, rnd[v] = round, clear the
@@ -113,7 +116,7 @@ __global__ void __launch_bounds__(kBlock) k_peel_compact(int32_t n, const int32_
                                                          uint32_t *__restrict__ alive, const int32_t *__restrict__ deg,
                                                          PeelView p, PeelState *st, int32_t *__restrict__ core,
                                                          int32_t *__restrict__ rnd, uint32_t *__restrict__ vis,
-                                                         int32_t *__restrict__ dlist)
+                                                         int32_t *__restrict__ dlist, int32_t *__restrict__ dcls)
 {
     const int lane = threadIdx.x & 31;
     const int32_t nw = (n + 31) >> 5;
@@ -125,9 +128,10 @@ __global__ void __launch_bounds__(kBlock) k_peel_compact(int32_t n, const int32_
         if (!aw) continue;  // warp-uniform
         const int32_t y = (int32_t)w * 32 + lane;
         bool del = false;
-        int32_t k = 0;
+        int32_t k = 0, gy = 0;
         if (y < n && ((aw >> lane) & 1u)) {
-            k = __ldg(&p.kg[graph_of(p, y)]);
+            gy = graph_of(p, y);
+            k = __ldg(&p.kg[gy]);
             del = deg[y] <= k;
         }
         const unsigned mask = __ballot_sync(kFull, del);
@@ -151,6 +155,14 @@ __global__ void __launch_bounds__(kBlock) k_peel_compact(int32_t n, const int32_
         }
         base = __shfl_sync(kFull, base, 0);
         if (del) dlist[base + __popc(mask & lanemask_lt())] = y;
+        // class regions of the deleted-source lists
+        const int32_t cy = del ? __ldg(&p.cls[gy]) : -1;
+        const int32_t c0 = __shfl_sync(kFull, cy, __ffs(mask) - 1);
+        if (__all_sync(kFull, !del || cy == c0)) {
+            warp_append(del, y, dcls + __ldg(&p.cls_off[c0]), &p.nDc[c0]);
+        } else if (del) {
+            dcls[__ldg(&p.cls_off[cy]) + atomicAdd(&p.nDc[cy], 1)] = y;
+        }
     }
 }
 
@@ -212,6 +224,22 @@ __global__ void __launch_bounds__(kBlock) k_affected_push(GraphView g, const uin
     }
 }
 
+__global__ void k_apply_dcount(const int32_t *__restrict__ list, int32_t inner, int32_t total,
+                               int32_t *__restrict__ dcount, int32_t *__restrict__ deg)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = list[i];
+        if (i >= inner) deg[u] -= dcount ? dcount[u] : 1;
+        if (dcount) dcount[u] = 0;
+    }
+}
+
+__global__ void k_snapshot_inner(PeelView p, const int32_t *__restrict__ cls_h, int lvl, int32_t *__restrict__ inner)
+{
+    for (int32_t c = threadIdx.x; c < p.ncls; c += blockDim.x)
+        if (cls_h[c] == lvl + 1) inner[c] = p.nAc[c];
+}
+
 // nA = sum over classes of the per-class counts (for the host).
 __global__ void k_sum_classes(PeelView p, PeelState *st)
 {
@@ -254,10 +282,19 @@ cudaError_t launch_set_level(const PeelView &p, PeelState *st, cudaStream_t s)
 }
 
 cudaError_t launch_peel_compact(const GraphView &g, uint32_t *alive, const int32_t *deg, const PeelView &p,
-                                PeelState *st, int32_t *core, int32_t *rnd, uint32_t *vis, int32_t *dlist, int grid,
+                                PeelState *st, int32_t *core, int32_t *rnd, uint32_t *vis, int32_t *dlist,
+                                int32_t *dcls, int grid, cudaStream_t s)
+{
+    k_peel_compact<<<grid, kBlock, 0, s>>>(g.n, g.row_ptr, alive, deg, p, st, core, rnd, vis, dlist, dcls);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_dcount(const int32_t *list, int32_t inner, int32_t total, int32_t *dcount, int32_t *deg,
                                 cudaStream_t s)
 {
-    k_peel_compact<<<grid, kBlock, 0, s>>>(g.n, g.row_ptr, alive, deg, p, st, core, rnd, vis, dlist);
+    if (total <= 0) return cudaSuccess;
+    const int blocks = (total + 511) / 512 < 2048 ? (total + 511) / 512 : 2048;
+    k_apply_dcount<<<blocks, 512, 0, s>>>(list, inner, total, dcount, deg);
     return cudaGetLastError();
 }
 
@@ -266,6 +303,12 @@ cudaError_t launch_affected_level(const GraphView &g, const uint32_t *alive, int
                                   cudaStream_t s)
 {
     k_affected_push<<<grid, kBlock, 0, s>>>(g, alive, lvl, aq[0], aq[1], aq[2], vis, p, st, A, last);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_snapshot_inner(const PeelView &p, const int32_t *cls_h, int lvl, int32_t *inner, cudaStream_t s)
+{
+    k_snapshot_inner<<<1, 256, 0, s>>>(p, cls_h, lvl, inner);
     return cudaGetLastError();
 }
 
