@@ -467,7 +467,6 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
     if ((s = ensure_bfs(c, W)) != KHCORE_OK) return s;
     const GraphView g = c->view();
     const int grid = bfs_grid(c, W);
-    const size_t nwb = (((size_t)c->n + 31) / 32) * sizeof(uint32_t);
 
     PeelView pv;
     pv.G = G;
@@ -521,7 +520,6 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         // the affected-BFS frontier lists reuse the BFS frontier lists Q[0..2]
         CU(launch_min_alive_deg(g, c->alive, c->deg, pv, grid, c->stream));
         CU(launch_set_level(pv, c->st, c->stream));
-        CU(cudaMemsetAsync(c->vis, 0, nwb, c->stream));
         CU(launch_peel_compact(g, c->alive, c->deg, pv, c->st, c->core, c->rnd, c->vis, c->Q[0], c->dcls, grid,
                                c->stream));
         stt.kernel_launches += 3;

@@ -110,8 +110,9 @@ __global__ void k_set_level(PeelView p, PeelState *st)
 }
 
 // D = {alive v : deg[v] <= k_g(v)}: core[v] = k, rnd[v] = round, clear the
-// alive bit, set v's bit in vis and append v to dlist (st->aq[0]). A warp
-// owns one 32-vertex word of each bitset.
+// alive bit, append v to dlist (st->aq[0]) and to its class region of dcls.
+// vis is rewritten whole: exactly the bits of D. A warp owns one 32-vertex
+// word of each bitset.
 __global__ void __launch_bounds__(kBlock) k_peel_compact(int32_t n, const int32_t *__restrict__ rp,
                                                          uint32_t *__restrict__ alive, const int32_t *__restrict__ deg,
                                                          PeelView p, PeelState *st, int32_t *__restrict__ core,
@@ -125,7 +126,10 @@ __global__ void __launch_bounds__(kBlock) k_peel_compact(int32_t n, const int32_
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t w = warp; w < nw; w += nwarps) {
         const uint32_t aw = alive[w];
-        if (!aw) continue;  // warp-uniform
+        if (!aw) {  // warp-uniform
+            if (lane == 0) vis[w] = 0;
+            continue;
+        }
         const int32_t y = (int32_t)w * 32 + lane;
         bool del = false;
         int32_t k = 0, gy = 0;
@@ -135,7 +139,10 @@ __global__ void __launch_bounds__(kBlock) k_peel_compact(int32_t n, const int32_
             del = deg[y] <= k;
         }
         const unsigned mask = __ballot_sync(kFull, del);
-        if (!mask) continue;  // warp-uniform
+        if (!mask) {  // warp-uniform
+            if (lane == 0) vis[w] = 0;
+            continue;
+        }
         unsigned long long dsum = 0;
         if (del) {
             core[y] = k;
@@ -147,7 +154,7 @@ __global__ void __launch_bounds__(kBlock) k_peel_compact(int32_t n, const int32_
         int32_t base = 0;
         if (lane == 0) {
             alive[w] = aw & ~mask;
-            vis[w] = mask;  // vis is zero before the launch
+            vis[w] = mask;  // every word of vis is written: it starts the round's affected BFS
             base = atomicAdd(&st->aq[0], __popc(mask));
             atomicAdd(&st->nD, __popc(mask));
             atomicSub(&st->alive, __popc(mask));
