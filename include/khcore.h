@@ -199,6 +199,25 @@ khcore_status khcore_set_words(khcore_ctx *ctx, int32_t words);
 khcore_status khcore_set_push_alpha(khcore_ctx *ctx, int32_t alpha);
 
 /*
+ * khcore_set_round_loop — how the peel rounds are driven.
+ *   0 (default)  the whole decomposition runs as one cooperative persistent
+ *                kernel; phases are separated by grid barriers and every
+ *                decision between them is taken on the device
+ *   1            the host launches each phase and reads the round's counts
+ *                back before planning the recompute
+ * Results are identical. EINVAL for other values.
+ */
+khcore_status khcore_set_round_loop(khcore_ctx *ctx, int32_t mode);
+
+/*
+ * khcore_set_wait_limit — time limit of one grid-barrier wait of the
+ * persistent kernel, in nanoseconds (default 10 s). A wait that runs out stops
+ * the decomposition with KHCORE_ETIMEOUT; the context stays usable and the
+ * next call starts from a clean state.
+ */
+khcore_status khcore_set_wait_limit(khcore_ctx *ctx, uint64_t ns);
+
+/*
  * khcore_set_profiling — when on (nonzero), every BFS level kernel launch is
  * bracketed by CUDA events on the context's stream and khcore_stats reports
  * their count, summed time and algorithmic bytes. Results do not change.

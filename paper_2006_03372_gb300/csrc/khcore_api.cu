@@ -63,6 +63,12 @@ struct khcore_ctx {
     int32_t *cnt = nullptr;
     unsigned long long *edges = nullptr;  // device counter of plain-BFS-equivalent edges
     int32_t push_alpha = 16;              // push when frontier degree sum * alpha < alive CSR entries
+    int32_t round_loop = 0;               // 0: one persistent launch per decomposition, 1: host-driven rounds
+    unsigned long long wait_limit_ns = 10ull * 1000 * 1000 * 1000;  // one grid-barrier wait
+    bool dirty = false;                   // a launch stopped midway: BFS buffers need clearing
+    int32_t *cls_size = nullptr;          // [G] initial class sizes (device)
+    GridSync *gs = nullptr;
+    PersistStats *pstats = nullptr;
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
@@ -243,6 +249,24 @@ khcore_status ensure_bfs(khcore_ctx *c, int W)
 
 int bfs_grid(khcore_ctx *c, int W) { return c->sm_count * max_blocks_per_sm_bfs(W); }
 
+// After a launch that stopped midway (a timed-out barrier) the BFS buffers may
+// hold rows of an unfinished batch: restore the all-zero state.
+khcore_status clear_if_dirty(khcore_ctx *c)
+{
+    if (!c->dirty || c->W_alloc == 0) return KHCORE_OK;
+    const size_t words = (size_t)std::max(c->n, 1) * c->W_alloc;
+    const size_t nflag = (((size_t)c->n + 3) / 4) * 4;
+    CU(cudaMemsetAsync(c->V, 0, words * sizeof(uint64_t), c->stream));
+    CU(cudaMemsetAsync(c->F[0], 0, words * sizeof(uint64_t), c->stream));
+    CU(cudaMemsetAsync(c->F[1], 0, words * sizeof(uint64_t), c->stream));
+    CU(cudaMemsetAsync(c->flag[0], 0, nflag, c->stream));
+    CU(cudaMemsetAsync(c->flag[1], 0, nflag, c->stream));
+    CU(cudaMemsetAsync(c->cnt, 0, (size_t)64 * c->W_alloc * sizeof(int32_t), c->stream));
+    CU(cudaMemsetAsync(c->dcount, 0, sizeof(int32_t) * (size_t)std::max(c->n, 1), c->stream));
+    c->dirty = false;
+    return KHCORE_OK;
+}
+
 // Sum the timed level launches recorded so far (waits for the last one).
 khcore_status flush_timer(khcore_ctx *c)
 {
@@ -394,6 +418,9 @@ khcore_status setup_ctx(khcore_ctx *c, const std::vector<int32_t> &rp, const std
     A(dev_alloc(&c->clsh, (size_t)c->G));
     A(dev_alloc(&c->dcls, (size_t)n));
     A(dev_alloc(&c->dcount, (size_t)n));
+    A(dev_alloc(&c->cls_size, (size_t)c->G));
+    A(dev_alloc(&c->gs, 1));
+    A(dev_alloc(&c->pstats, 1));
     if (c->G > 1) A(dev_alloc(&c->gid, (size_t)n));
     if (st != KHCORE_OK) return st;
     e = cudaMallocHost((void **)&c->st_host, sizeof(PeelState));
@@ -415,6 +442,41 @@ khcore_status setup_ctx(khcore_ctx *c, const std::vector<int32_t> &rp, const std
     if (e == cudaSuccess) e = cudaMemsetAsync(c->flag[1], 0, nflag, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return fail(nullptr, KHCORE_ECUDA, "graph upload: %s", cudaGetErrorString(e));
+    return KHCORE_OK;
+}
+
+// Outputs and statistics common to both round loops. persistent: the level
+// time is the whole launch (one kernel).
+khcore_status finish_decompose(khcore_ctx *c, int32_t G, int32_t *core_out, int32_t *round_out, khcore_stats *stats,
+                               khcore_stats stt, bool persistent)
+{
+    khcore_status s;
+    CU(cudaEventRecord(c->ev1, c->stream));
+    if ((s = write_out(c, core_out, c->core)) != KHCORE_OK) return s;
+    if ((s = write_out(c, round_out, c->rnd)) != KHCORE_OK) return s;
+    unsigned long long edges = 0;
+    std::vector<int32_t> kg(G);
+    CU(cudaMemcpyAsync(&edges, c->edges, sizeof edges, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(kg.data(), c->kg, sizeof(int32_t) * G, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    stt.device_ms = ms;
+    stt.edges_traversed = (int64_t)edges;
+    stt.k_max = *std::max_element(kg.begin(), kg.end());
+    if (persistent) {
+        stt.level_ms = c->profiling ? ms : 0.0;
+    } else {
+        if ((s = flush_timer(c)) != KHCORE_OK) return s;
+        stt.level_ms = c->level_ms;
+        stt.level_launches = c->level_launches;
+    }
+    if (!c->profiling) {
+        stt.level_bytes = 0;
+        stt.level_ms = 0;
+        stt.level_launches = 0;
+    }
+    if (stats) *stats = stt;
     return KHCORE_OK;
 }
 
@@ -465,6 +527,7 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
     stt.words_per_vertex = W;
     khcore_status s;
     if ((s = ensure_bfs(c, W)) != KHCORE_OK) return s;
+    if ((s = clear_if_dirty(c)) != KHCORE_OK) return s;
     const GraphView g = c->view();
     const int grid = bfs_grid(c, W);
 
@@ -497,6 +560,8 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
     CU(cudaMemcpyAsync(c->gcls, gcls.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemcpyAsync(c->cls_off, cls_off.data(), sizeof(int32_t) * ncls, cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemcpyAsync(c->clsh, cls_h.data(), sizeof(int32_t) * ncls, cudaMemcpyHostToDevice, c->stream));
+    std::vector<int32_t> cls_size32(cls_size.begin(), cls_size.end());
+    CU(cudaMemcpyAsync(c->cls_size, cls_size32.data(), sizeof(int32_t) * ncls, cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemsetAsync(c->inner, 0, sizeof(int32_t) * ncls, c->stream));
     CU(cudaMemcpyAsync(c->cls_src, cls_src.data(), sizeof(int32_t) * c->n, cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemsetAsync(c->edges, 0, sizeof(unsigned long long), c->stream));
@@ -504,6 +569,73 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
     stt.kernel_launches += 1;
     // the host vectors above must outlive the async copies
     CU(cudaStreamSynchronize(c->stream));
+
+    const int pgrid = c->round_loop == 0 ? c->sm_count * max_blocks_per_sm_persist(W) : 0;
+    if (pgrid > 0) {
+        // the whole decomposition in one cooperative launch
+        PersistLaunch L;
+        L.g = g;
+        L.alive = c->alive;
+        L.deg = c->deg;
+        L.core = c->core;
+        L.rnd = c->rnd;
+        L.p = pv;
+        L.st = c->st;
+        L.b.V = c->V;
+        L.b.F[0] = c->F[0];
+        L.b.F[1] = c->F[1];
+        L.b.flag[0] = c->flag[0];
+        L.b.flag[1] = c->flag[1];
+        for (int k = 0; k < 3; k++) {
+            L.b.Q[k] = c->Q[k];
+            L.b.QH[k] = c->QH[k];
+            L.aq[k] = c->Q[k];  // the affected-BFS ring reuses the BFS frontier lists
+        }
+        L.b.T = c->T;
+        L.b.ctl = c->ctl;
+        L.b.cnt = c->cnt;
+        L.b.edges = c->edges;
+        L.b.rowcnt = nullptr;
+        L.vis = c->vis;
+        L.A = c->src;
+        L.dcls = c->dcls;
+        L.cls_src = c->cls_src;
+        L.cls_h = c->clsh;
+        L.cls_size = c->cls_size;
+        L.cls_off = c->cls_off;
+        L.inner = c->inner;
+        L.dcount = c->dcount;
+        L.ncls = ncls;
+        L.hmax = hmax;
+        L.alpha = c->push_alpha;
+        L.gs = c->gs;
+        L.ps = c->pstats;
+        L.timeout_ns = c->wait_limit_ns;
+        CU(cudaMemsetAsync(c->gs, 0, sizeof(GridSync), c->stream));
+        CU(cudaMemsetAsync(c->pstats, 0, sizeof(PersistStats), c->stream));
+        CU(launch_decompose_persist(W, L, pgrid, c->stream));
+        GridSync gsh;
+        PersistStats psh;
+        CU(cudaMemcpyAsync(&gsh, c->gs, sizeof gsh, cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaMemcpyAsync(&psh, c->pstats, sizeof psh, cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        if (gsh.err) {
+            c->dirty = true;
+            return fail(c, KHCORE_ETIMEOUT, "a grid-barrier wait exceeded %.3f s; the decomposition stopped",
+                        (double)c->wait_limit_ns * 1e-9);
+        }
+        stt.kernel_launches += 1;
+        stt.rounds = (int32_t)psh.rounds;
+        stt.source_batches += psh.source_batches;
+        stt.recomputed_total += psh.recomputed_total;
+        stt.deleted_total += psh.deleted_total;
+        stt.affected_total += psh.affected_total;
+        if (c->profiling) {
+            stt.level_bytes = psh.level_bytes;
+            stt.level_launches = psh.level_steps;
+        }
+        return finish_decompose(c, G, core_out, round_out, stats, stt, true);
+    }
 
     // initial h-degrees, class by class
     for (int32_t k = 0; k < ncls; k++)
@@ -579,25 +711,7 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         CU(cudaMemcpyAsync(&c->st->round, &c->st_host->round, sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
     }
     stt.rounds = round;
-    CU(cudaEventRecord(c->ev1, c->stream));
-    if ((s = write_out(c, core_out, c->core)) != KHCORE_OK) return s;
-    if ((s = write_out(c, round_out, c->rnd)) != KHCORE_OK) return s;
-    unsigned long long edges = 0;
-    std::vector<int32_t> kg(G);
-    CU(cudaMemcpyAsync(&edges, c->edges, sizeof edges, cudaMemcpyDeviceToHost, c->stream));
-    CU(cudaMemcpyAsync(kg.data(), c->kg, sizeof(int32_t) * G, cudaMemcpyDeviceToHost, c->stream));
-    CU(cudaStreamSynchronize(c->stream));
-    float ms = 0.f;
-    CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
-    stt.device_ms = ms;
-    stt.edges_traversed = (int64_t)edges;
-    stt.k_max = *std::max_element(kg.begin(), kg.end());
-    if ((s = flush_timer(c)) != KHCORE_OK) return s;
-    stt.level_ms = c->level_ms;
-    stt.level_launches = c->level_launches;
-    if (!c->profiling) stt.level_bytes = 0;
-    if (stats) *stats = stt;
-    return KHCORE_OK;
+    return finish_decompose(c, G, core_out, round_out, stats, stt, false);
 }
 
 khcore_status create_common(int32_t G, const std::vector<int64_t> &v_off, std::vector<int32_t> &rp,
@@ -649,7 +763,7 @@ void khcore_destroy(khcore_ctx *c)
     cudaSetDevice(c->device);
     if (c->stream && !c->failed) cudaStreamSynchronize(c->stream);
     void *bufs[] = {c->row_ptr, c->col, c->classes, c->gid, c->kg, c->ming, c->hg, c->gcls, c->cls_off, c->nAc,
-                    c->nDc, c->inner, c->clsh, c->dcls, c->dcount,
+                    c->nDc, c->inner, c->clsh, c->dcls, c->dcount, c->cls_size, c->gs, c->pstats,
                     c->cls_src, c->alive, c->deg, c->core, c->rnd, c->src, c->vis, c->st, c->V, c->F[0], c->F[1],
                     c->flag[0], c->flag[1], c->Q[0], c->Q[1], c->Q[2], c->QH[0], c->QH[1], c->QH[2], c->T, c->ctl,
                     c->cnt, c->edges};
@@ -756,6 +870,21 @@ khcore_status khcore_set_push_alpha(khcore_ctx *c, int32_t alpha)
     return KHCORE_OK;
 }
 
+khcore_status khcore_set_round_loop(khcore_ctx *c, int32_t mode)
+{
+    if (!c) return KHCORE_EINVAL;
+    if (mode != 0 && mode != 1) return fail(c, KHCORE_EINVAL, "mode must be 0 (device) or 1 (host), got %d", mode);
+    c->round_loop = mode;
+    return KHCORE_OK;
+}
+
+khcore_status khcore_set_wait_limit(khcore_ctx *c, uint64_t ns)
+{
+    if (!c) return KHCORE_EINVAL;
+    c->wait_limit_ns = ns;
+    return KHCORE_OK;
+}
+
 khcore_status khcore_set_profiling(khcore_ctx *c, int32_t on)
 {
     if (!c) return KHCORE_EINVAL;
@@ -783,6 +912,7 @@ khcore_status khcore_hdegrees(khcore_ctx *c, int32_t h, int32_t *deg_out)
     if (c->n == 0) return KHCORE_OK;
     const int W = c->W_req ? c->W_req : auto_words(c->n);
     if ((s = ensure_bfs(c, W)) != KHCORE_OK) return s;
+    if ((s = clear_if_dirty(c)) != KHCORE_OK) return s;
     int32_t hmax = 1;
     for (int32_t g = 0; g < c->G; g++) hmax = std::max(hmax, effective_h(c->v_off[g + 1] - c->v_off[g], h));
     CU(launch_alive_init(c->alive, c->n, c->stream));
@@ -813,6 +943,7 @@ khcore_status khcore_hdegrees_of(khcore_ctx *c, int32_t h, int32_t count, const 
     }
     const int W = c->W_req ? c->W_req : auto_words(c->n);
     if ((s = ensure_bfs(c, W)) != KHCORE_OK) return s;
+    if ((s = clear_if_dirty(c)) != KHCORE_OK) return s;
     int32_t hmax = 1;
     for (int32_t g = 0; g < c->G; g++) hmax = std::max(hmax, effective_h(c->v_off[g + 1] - c->v_off[g], h));
     CU(launch_alive_init(c->alive, c->n, c->stream));

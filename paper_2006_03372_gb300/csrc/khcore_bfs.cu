@@ -1,586 +1,35 @@
-// khcore_bfs.cu — multi-source h-bounded BFS on sm_103a: the h-hop degree
-// d_v^h of Sec. II for a batch of 64*W sources at once.
-//
-// Each vertex holds W 64-bit words per state array; bit b of word j stands
-// for source 64*j+b of the batch (the paper packs 64 set members per 64-bit
-// word in its Reach bitmaps, Sec. IV-B; here the members are BFS sources).
-// A level turns the frontier F (sources that reached a vertex at exactly the
-// current distance) into the next one, in one of two directions chosen on the
-// device from the frontier's degree sum:
-//   pull  every alive y: new(y) = OR_{x in N(y), x in frontier} F(x), minus V(y);
-//   push  every frontier x, every alive neighbour y: F'(y) |= F(x) & ~V(y)
-//         with atomicOr, whose returned old value tells which bits are new.
-// The number of newly reached vertices per source is a column count over the
-// new words, kept per lane in byte-sliced (SWAR) counters. The h-degree of a
-// source is the total count over its h levels.
-#include <climits>
-#include <cstdint>
-
-#include "khcore_internal.cuh"
+// khcore_bfs.cu — per-phase kernels of the multi-source h-bounded BFS (one
+// launch per phase, host-driven) and their launcher. The device code lives in
+// khcore_device.cuh.
+#include "khcore_device.cuh"
 
 namespace khc {
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ bool is_alive(const uint32_t *alive, int32_t y)
-{
-    return (__ldg(&alive[y >> 5]) >> (y & 31)) & 1u;
-}
-
-__device__ __forceinline__ unsigned lanemask_lt()
-{
-    unsigned m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
-
-// Kernel parameters indexed with a runtime value would be copied to local
-// memory; pick array members with selects instead.
-template <class T>
-__device__ __forceinline__ T pick2(const T (&a)[2], int i)
-{
-    return i ? a[1] : a[0];
-}
-template <class T>
-__device__ __forceinline__ T pick3(const T (&a)[3], int i)
-{
-    return i == 0 ? a[0] : (i == 1 ? a[1] : a[2]);
-}
-
-// Whole warp calls; lanes with pred append val to list (warp-aggregated).
-__device__ __forceinline__ void warp_append(bool pred, int32_t val, int32_t *list, int32_t *counter)
-{
-    const unsigned m = __ballot_sync(kFull, pred);
-    if (!m) return;
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(m) - 1;
-    int32_t base = 0;
-    if (lane == leader) base = atomicAdd(counter, __popc(m));
-    base = __shfl_sync(kFull, base, leader);
-    if (pred) list[base + __popc(m & lanemask_lt())] = val;
-}
-
-// Byte test-and-set on a uint8 flag array through its 32-bit word.
-__device__ __forceinline__ bool flag_claim(uint8_t *flags, int32_t y)
-{
-    unsigned *word = reinterpret_cast<unsigned *>(flags + (y & ~3));
-    const unsigned bit = 1u << (8 * (y & 3));
-    return (atomicOr(word, bit) & bit) == 0;
-}
-
-// Byte-sliced column counters: byte k of a[t] counts bit 8k+t of the words
-// added. Each add contributes at most 1 per byte, so a flush every 255 adds
-// keeps the bytes exact.
-struct Swar {
-    uint64_t a[8];
-    int n;
-    __device__ __forceinline__ void reset()
-    {
-#pragma unroll
-        for (int t = 0; t < 8; t++) a[t] = 0;
-        n = 0;
-    }
-    __device__ __forceinline__ void add(uint64_t w)
-    {
-#pragma unroll
-        for (int t = 0; t < 8; t++) a[t] += (w >> t) & 0x0101010101010101ull;
-    }
-};
-
-// Whole warp calls. Lanes with the same word index j = lane % W are summed
-// (16-bit lanes cannot overflow: at most 32 * 255), then lane j adds its 64
-// column counts to cnt_s[64*j + bit].
 template <int W>
-__device__ __forceinline__ void swar_flush(Swar &s, int32_t *cnt_s)
+__global__ void k_seed(const int32_t *src, int32_t ns, BfsBufs b, const int32_t *rp)
 {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int t = 0; t < 8; t++) {
-        uint64_t lo = s.a[t] & 0x00FF00FF00FF00FFull;         // bytes 0,2,4,6
-        uint64_t hi = (s.a[t] >> 8) & 0x00FF00FF00FF00FFull;  // bytes 1,3,5,7
-#pragma unroll
-        for (int off = W; off < 32; off <<= 1) {
-            lo += __shfl_xor_sync(kFull, lo, off);
-            hi += __shfl_xor_sync(kFull, hi, off);
-        }
-        if (lane < W) {
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const uint32_t c0 = (uint32_t)(lo >> (16 * k)) & 0xffffu;  // byte 2k   -> bit 16k+t
-                const uint32_t c1 = (uint32_t)(hi >> (16 * k)) & 0xffffu;  // byte 2k+1 -> bit 16k+8+t
-                if (c0) atomicAdd(&cnt_s[lane * 64 + 16 * k + t], (int32_t)c0);
-                if (c1) atomicAdd(&cnt_s[lane * 64 + 16 * k + 8 + t], (int32_t)c1);
-            }
-        }
-        s.a[t] = 0;
-    }
-    s.n = 0;
+    dev_seed<W>(src, ns, b, rp);
 }
 
-template <int W>
-__device__ __forceinline__ void swar_step(Swar &s, uint64_t w, int32_t *cnt_s)
-{
-    s.add(w);
-    if (++s.n == 255) swar_flush<W>(s, cnt_s);
-}
-
-// Per-thread accumulators flushed once at the end of a level kernel.
-struct Acc {
-    unsigned long long scanned;  // plain-BFS-equivalent CSR entries
-    unsigned long long fe;       // degree sum of vertices appended to the next frontier
-};
-
-__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
-{
-#pragma unroll
-    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
-    return v;
-}
-
-__device__ __forceinline__ bool use_push(const LevelCtl *ctl, int slot, BfsTuning tune)
-{
-    return tune.alpha > 0 &&
-           (unsigned long long)ctl->fe[slot] * (unsigned long long)tune.alpha < tune.m_alive;
-}
-
-// Append y (already claimed in the next frontier) to Q, and to QH if heavy.
-// Whole warp calls; pred marks the lanes that append.
-__device__ __forceinline__ void append_frontier(bool pred, int32_t y, int32_t deg, const BfsBufs &b,
-                                                int nslot, Acc &acc)
-{
-    warp_append(pred, y, pick3(b.Q, nslot), &b.ctl->q[nslot]);
-    warp_append(pred && deg > kPushChunk, y, pick3(b.QH, nslot), &b.ctl->qh[nslot]);
-    if (pred) acc.fe += (unsigned long long)deg;
-}
-
-
-// OR the W words of frontier row x into a.
-template <int W>
-__device__ __forceinline__ void or_row(uint64_t (&a)[W], const uint64_t *__restrict__ F, int32_t x)
-{
-    if constexpr (W == 1) {
-        a[0] |= __ldg(F + x);
-    } else {
-        const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(F + (size_t)x * W);
-#pragma unroll
-        for (int k = 0; k < W / 2; k++) {
-            const ulonglong2 v = __ldg(p + k);
-            a[2 * k] |= v.x;
-            a[2 * k + 1] |= v.y;
-        }
-    }
-}
-
-// Edges e = first, first+stride, ... < e1: OR the rows of flagged neighbours
-// into a. Two edges per step so that each lane keeps two independent
-// col -> flag -> row chains in flight.
-template <int W>
-__device__ __forceinline__ void gather_edges(uint64_t (&a)[W], const int32_t *__restrict__ col,
-                                             const uint8_t *__restrict__ flc, const uint64_t *__restrict__ Fc,
-                                             int32_t first, int32_t e1, int32_t stride)
-{
-    int32_t e = first;
-    for (; e + stride < e1; e += 2 * stride) {
-        const int32_t x0 = __ldg(&col[e]);
-        const int32_t x1 = __ldg(&col[e + stride]);
-        const uint8_t f0 = __ldg(&flc[x0]);
-        const uint8_t f1 = __ldg(&flc[x1]);
-        if (f0) or_row<W>(a, Fc, x0);
-        if (f1) or_row<W>(a, Fc, x1);
-    }
-    if (e < e1) {
-        const int32_t x0 = __ldg(&col[e]);
-        if (__ldg(&flc[x0])) or_row<W>(a, Fc, x0);
-    }
-}
-
-// OR a across the G lanes of each aligned lane group (G a power of two <= 32).
-template <int W, int G>
-__device__ __forceinline__ void group_or(uint64_t (&a)[W])
-{
-#pragma unroll
-    for (int off = 1; off < G; off <<= 1) {
-#pragma unroll
-        for (int k = 0; k < W; k++) a[k] |= __shfl_xor_sync(kFull, a[k], off);
-    }
-}
-
-// a[i] without dynamic register indexing.
-template <int W>
-__device__ __forceinline__ uint64_t select_word(const uint64_t (&a)[W], int i)
-{
-    uint64_t r = 0;
-#pragma unroll
-    for (int k = 0; k < W; k++)
-        if (k == i) r = a[k];
-    return r;
-}
-
-// ---------------------------------------------------------------------------
-// level 0: sources. One block of up to 1024 threads; resets the level ring.
-// ---------------------------------------------------------------------------
-template <int W>
-__global__ void k_seed(const int32_t *__restrict__ src, int32_t ns, BfsBufs b, const int32_t *__restrict__ rp)
-{
-    __shared__ unsigned long long s_fe;
-    const int i = threadIdx.x;
-    if (i == 0) {
-        for (int k = 0; k < 3; k++) {
-            b.ctl->q[k] = 0;
-            b.ctl->qh[k] = 0;
-            b.ctl->fe[k] = 0;
-        }
-        b.ctl->t = 0;
-        s_fe = 0;
-    }
-    __syncthreads();
-    unsigned long long d = 0;
-    int32_t s = -1;
-    if (i < ns) {
-        s = src[i];
-        d = (unsigned long long)(rp[s + 1] - rp[s]);
-        const int word = i >> 6;
-        const uint64_t bit = 1ull << (i & 63);
-        b.V[(size_t)s * W + word] = bit;  // V(s) is zero between batches
-        b.F[0][(size_t)s * W + word] = bit;  // F rows are zero between batches
-        b.flag[0][s] = 1;
-        b.Q[0][i] = s;
-        b.T[i] = s;
-    }
-    warp_append(i < ns && d > (unsigned long long)kPushChunk, s, b.QH[0], &b.ctl->qh[0]);
-    const unsigned long long ws = warp_sum(d);
-    if ((i & 31) == 0 && ws) atomicAdd(&s_fe, ws);
-    __syncthreads();
-    if (i == 0) {
-        b.ctl->q[0] = ns;
-        b.ctl->t = ns;
-        b.ctl->fe[0] = s_fe;
-        if (s_fe) atomicAdd(b.edges, s_fe);  // every source scans its own row
-    }
-}
-
-
-// Non-last levels: store the new words of vertex y (lanes gi < W of its
-// group hold word gi), mark it in the next frontier, append it to Q (and T
-// on its first visit). Whole warp calls.
-template <int W, int G>
-__device__ __forceinline__ void finish_vertex(bool act, int32_t y, int32_t dy, uint64_t nw, uint64_t v, int gi,
-                                              int grp, uint64_t *__restrict__ V, uint64_t *__restrict__ Fn,
-                                              uint8_t *__restrict__ fln, const BfsBufs &b, int nslot, Acc &acc)
-{
-    const unsigned gmask = (G == 32) ? kFull : ((1u << G) - 1u);
-    const unsigned any = __ballot_sync(kFull, nw != 0);
-    const unsigned vany = __ballot_sync(kFull, v != 0);
-    const bool gany = ((any >> (grp * G)) & gmask) != 0;
-    const bool gv = ((vany >> (grp * G)) & gmask) != 0;
-    if (act && gany && gi < W) {
-        Fn[(size_t)y * W + gi] = nw;
-        if (nw) V[(size_t)y * W + gi] = v | nw;
-        acc.scanned += (unsigned long long)__popcll(nw) * (unsigned long long)dy;
-    }
-    const bool lead = act && gany && gi == 0;
-    if (lead) fln[y] = 1;
-    append_frontier(lead, y, dy, b, nslot, acc);
-    warp_append(lead && !gv, y, b.T, &b.ctl->t);
-}
-
-// Pull over a vertex list with G lanes per vertex (32/G vertices per warp).
-template <int W, int G, bool LAST>
-__device__ __forceinline__ void pull_groups(const int32_t *__restrict__ list, int32_t count, int64_t warp,
-                                            int64_t nwarps, const GraphView &g, const uint32_t *__restrict__ alive,
-                                            uint64_t *__restrict__ V, const uint64_t *__restrict__ Fc,
-                                            const uint8_t *__restrict__ flc, uint64_t *__restrict__ Fn,
-                                            uint8_t *__restrict__ fln, const BfsBufs &b, int nslot, Swar &sw,
-                                            int32_t *cnt_s, Acc &acc)
-{
-    static_assert(G >= W && 32 % G == 0, "group");
-    constexpr int VPW = 32 / G;
-    const int lane = threadIdx.x & 31;
-    const int gi = lane % G;
-    const int grp = lane / G;
-    const int32_t *__restrict__ rp = g.row_ptr;
-    for (int64_t base = warp * VPW; base < count; base += nwarps * VPW) {  // warp-uniform
-        const int64_t idx = base + grp;
-        int32_t y = -1, dy = 0;
-        bool act = false;
-        uint64_t a[W];
-#pragma unroll
-        for (int k = 0; k < W; k++) a[k] = 0;
-        if (idx < count) {
-            y = list[idx];
-            if (is_alive(alive, y)) {
-                act = true;
-                const int32_t e0 = rp[y], e1 = rp[y + 1];
-                dy = e1 - e0;
-                gather_edges<W>(a, g.col, flc, Fc, e0 + gi, e1, G);
-            }
-        }
-        group_or<W, G>(a);
-        uint64_t nw = 0, v = 0;
-        if (act && gi < W) {
-            v = V[(size_t)y * W + gi];
-            nw = select_word<W>(a, gi) & ~v;
-        }
-        swar_step<W>(sw, nw, cnt_s);
-        if (b.rowcnt) {  // uniform
-            int32_t rc = __popcll(nw);
-#pragma unroll
-            for (int off = 1; off < G; off <<= 1) rc += __shfl_xor_sync(kFull, rc, off);
-            if (act && gi == 0 && rc) atomicAdd(&b.rowcnt[y], rc);
-        }
-        if (!LAST) finish_vertex<W, G>(act, y, dy, nw, v, gi, grp, V, Fn, fln, b, nslot, acc);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// One level (lvl = 0-based distance of the frontier being expanded).
-// LAST: the expansion reaching distance h; only counts (pull) or counts and
-// records the rows to clear (push).
-// ---------------------------------------------------------------------------
 template <int W, bool LAST>
-__global__ void __launch_bounds__(kBlock) k_level(GraphView g, const uint32_t *__restrict__ alive, BfsBufs b,
-                                                  int lvl, BfsTuning tune)
+__global__ void __launch_bounds__(kBlock) k_level(GraphView g, const uint32_t *alive, BfsBufs b, int lvl,
+                                                  BfsTuning tune)
 {
-    static_assert(W == 1 || W == 2 || W == 4 || W == 8 || W == 16, "W");
-    __shared__ int32_t cnt_s[64 * W];
-    __shared__ uint64_t red[kBlock / 32][W];
-
-    const int cslot = lvl % 3, nslot = (lvl + 1) % 3;
-    const int cb = lvl & 1, nb_ = cb ^ 1;
-    const uint64_t *__restrict__ Fc = pick2(b.F, cb);
-    const uint8_t *__restrict__ flc = pick2(b.flag, cb);
-    uint64_t *__restrict__ Fn = pick2(b.F, nb_);
-    uint8_t *__restrict__ fln = pick2(b.flag, nb_);
-    uint64_t *__restrict__ V = b.V;
-    const bool push = use_push(b.ctl, cslot, tune);
-
-    for (int i = threadIdx.x; i < 64 * W; i += blockDim.x) cnt_s[i] = 0;
-    __syncthreads();
-
-    const int lane = threadIdx.x & 31;
-    const int j = lane % W;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int32_t *__restrict__ rp = g.row_ptr;
-    const int32_t *__restrict__ col = g.col;
-    Swar sw;
-    sw.reset();
-    Acc acc{0, 0};
-
-    if (push) {
-        // ---------------- push: frontier vertices scatter to neighbours ----
-        constexpr int SLOTS = 32 / W;
-        const int slot = lane / W;
-        const int grp = slot;
-        const unsigned gmask = (1u << W) - 1u;
-        const int32_t nq = b.ctl->q[cslot];
-        const int32_t nqh = b.ctl->qh[cslot];
-        const int32_t *__restrict__ Qc = pick3(b.Q, cslot);
-        const int32_t *__restrict__ QHc = pick3(b.QH, cslot);
-        // one edge of the expansion: y = col[e] gets fx & ~V(y)
-        auto edge = [&](int32_t e, int32_t e1, uint64_t fx) {
-            int32_t y = -1;
-            uint64_t nbits = 0, fresh = 0;
-            if (e < e1) {
-                y = __ldg(&col[e]);
-                if (is_alive(alive, y)) {
-                    nbits = fx & ~V[(size_t)y * W + j];
-                    if (nbits) {
-                        const unsigned long long old =
-                            atomicOr(reinterpret_cast<unsigned long long *>(&Fn[(size_t)y * W + j]),
-                                     (unsigned long long)nbits);
-                        fresh = nbits & ~(uint64_t)old;
-                        if (b.rowcnt && fresh) atomicAdd(&b.rowcnt[y], __popcll(fresh));
-                    }
-                }
-            }
-            swar_step<W>(sw, fresh, cnt_s);
-            const unsigned any = __ballot_sync(kFull, nbits != 0);
-            const bool lead = (j == 0) && (((any >> (grp * W)) & gmask) != 0);
-            bool claimed = false;
-            int32_t dy = 0;
-            if (lead) {
-                claimed = flag_claim(fln, y);
-                dy = rp[y + 1] - rp[y];
-            }
-            append_frontier(claimed, y, dy, b, nslot, acc);
-        };
-        // light frontier vertices: one warp each
-        for (int64_t i = warp; i < nq; i += nwarps) {
-            const int32_t x = Qc[i];
-            const int32_t e0 = rp[x], e1 = rp[x + 1];
-            if (e1 - e0 > kPushChunk) continue;  // warp-uniform; handled below
-            const uint64_t fx = Fc[(size_t)x * W + j];
-            for (int32_t eb = e0; eb < e1; eb += SLOTS) edge(eb + slot, e1, fx);
-        }
-        // heavy frontier vertices: every warp of the grid takes a share
-        for (int32_t k = 0; k < nqh; k++) {
-            const int32_t x = QHc[k];
-            const int32_t e1 = rp[x + 1];
-            const uint64_t fx = Fc[(size_t)x * W + j];
-            for (int64_t eb = rp[x] + warp * SLOTS; eb < e1; eb += nwarps * SLOTS)
-                edge((int32_t)eb + slot, e1, fx);
-        }
-    } else {
-        // ---------------- pull: every alive vertex gathers its neighbours ----
-        // A group of G lanes takes one vertex; each lane walks its own share
-        // of the edges (two independent chains per lane), ORs whole frontier
-        // rows into a[0..W-1], and the group ORs the lanes together. Lane
-        // gi < W of the group then finishes word gi.
-        // light (deg <= kLightMax): G = max(8, W) lanes per vertex
-        pull_groups<W, (W > 8 ? W : 8), LAST>(g.light, g.n_light, warp, nwarps, g, alive, V, Fc, flc, Fn, fln,
-                                              b, nslot, sw, cnt_s, acc);
-        // medium (deg <= kMediumMax): one warp per vertex
-        pull_groups<W, 32, LAST>(g.medium, g.n_medium, warp, nwarps, g, alive, V, Fc, flc, Fn, fln, b, nslot,
-                                 sw, cnt_s, acc);
-        // heavy: one block per vertex
-        {
-            const int wid = threadIdx.x >> 5;
-            const int nwarp_blk = blockDim.x >> 5;
-            for (int64_t i = blockIdx.x; i < g.n_heavy; i += gridDim.x) {
-                const int32_t y = g.heavy[i];
-                const bool act = is_alive(alive, y);  // block-uniform
-                const int32_t e0 = rp[y], e1 = rp[y + 1];
-                if (act) {
-                    uint64_t a[W];
-#pragma unroll
-                    for (int k = 0; k < W; k++) a[k] = 0;
-                    gather_edges<W>(a, col, flc, Fc, e0 + (int32_t)threadIdx.x, e1, (int32_t)blockDim.x);
-                    group_or<W, 32>(a);
-                    if (lane < W) red[wid][lane] = select_word<W>(a, lane);
-                }
-                __syncthreads();
-                if (wid == 0) {
-                    uint64_t nw = 0, v = 0;
-                    if (act && lane < W) {
-                        uint64_t m = 0;
-                        for (int w = 0; w < nwarp_blk; w++) m |= red[w][lane];
-                        v = V[(size_t)y * W + j];
-                        nw = m & ~v;
-                    }
-                    swar_step<W>(sw, nw, cnt_s);
-                    if (b.rowcnt) {
-                        int32_t rc = __popcll(nw);
-#pragma unroll
-                        for (int off = 1; off < 32; off <<= 1) rc += __shfl_xor_sync(kFull, rc, off);
-                        if (act && lane == 0 && rc) atomicAdd(&b.rowcnt[y], rc);
-                    }
-                    if (!LAST) finish_vertex<W, 32>(act, y, e1 - e0, nw, v, lane, 0, V, Fn, fln, b, nslot, acc);
-                }
-                __syncthreads();
-            }
-        }
-    }
-
-    swar_flush<W>(sw, cnt_s);
-    const unsigned long long sc = warp_sum(acc.scanned);
-    const unsigned long long fe = warp_sum(acc.fe);
-    if (lane == 0) {
-        if (sc) atomicAdd(b.edges, sc);
-        if (fe) atomicAdd(&b.ctl->fe[nslot], fe);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < 64 * W; i += blockDim.x) {
-        const int32_t c = cnt_s[i];
-        if (c) atomicAdd(&b.cnt[i], c);
-    }
+    dev_level<W, LAST>(g, alive, b, lvl, tune);
 }
 
-// ---------------------------------------------------------------------------
-// After level lvl: (push) fold the next frontier into V; clear the rows of the
-// expanded frontier (and, at the last level, of the next one); reset the ring
-// slot two levels ahead.
-// ---------------------------------------------------------------------------
 template <int W, bool LAST>
 __global__ void __launch_bounds__(kBlock) k_post(GraphView g, BfsBufs b, int lvl, BfsTuning tune)
 {
-    const int cslot = lvl % 3, nslot = (lvl + 1) % 3, oslot = (lvl + 2) % 3;
-    const int cb = lvl & 1, nb_ = cb ^ 1;
-    const bool push = use_push(b.ctl, cslot, tune);
-    const int lane = threadIdx.x & 31;
-    const int j = lane % W;
-    const int grp = lane / W;
-    constexpr int VPW = 32 / W;
-    const unsigned gmask = (1u << W) - 1u;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int32_t *__restrict__ rp = g.row_ptr;
-    unsigned long long scanned = 0;
-
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        b.ctl->q[oslot] = 0;
-        b.ctl->qh[oslot] = 0;
-        b.ctl->fe[oslot] = 0;
-    }
-    const int32_t nq = b.ctl->q[cslot];
-    const int32_t nn = b.ctl->q[nslot];
-    const int32_t *__restrict__ Qc = pick3(b.Q, cslot);
-    const int32_t *__restrict__ Qn = pick3(b.Q, nslot);
-    uint64_t *__restrict__ Fc = pick2(b.F, cb);
-    uint64_t *__restrict__ Fn = pick2(b.F, nb_);
-    uint8_t *__restrict__ flc = pick2(b.flag, cb);
-    uint8_t *__restrict__ fln = pick2(b.flag, nb_);
-
-    // clear the expanded frontier's rows
-    for (int64_t base = warp * VPW; base < nq; base += nwarps * VPW) {
-        const int64_t idx = base + grp;
-        if (idx < nq) {
-            const int32_t x = Qc[idx];
-            Fc[(size_t)x * W + j] = 0;
-            if (j == 0) flc[x] = 0;
-        }
-    }
-    if (push) {
-        for (int64_t base = warp * VPW; base < nn; base += nwarps * VPW) {
-            const int64_t idx = base + grp;
-            int32_t y = -1;
-            uint64_t f = 0, v = 0;
-            if (idx < nn) {
-                y = Qn[idx];
-                f = Fn[(size_t)y * W + j];
-                if (LAST) {
-                    Fn[(size_t)y * W + j] = 0;
-                    if (j == 0) fln[y] = 0;
-                } else {
-                    v = b.V[(size_t)y * W + j];
-                    if (f) b.V[(size_t)y * W + j] = v | f;
-                    scanned += (unsigned long long)__popcll(f) * (unsigned long long)(rp[y + 1] - rp[y]);
-                }
-            }
-            if (!LAST) {
-                const unsigned vany = __ballot_sync(kFull, v != 0);
-                const bool gv = ((vany >> (grp * W)) & gmask) != 0;
-                warp_append(idx < nn && j == 0 && !gv, y, b.T, &b.ctl->t);
-            }
-        }
-    }
-    scanned = warp_sum(scanned);
-    if (lane == 0 && scanned) atomicAdd(b.edges, scanned);
+    dev_post<W, LAST>(g, b, lvl, tune);
 }
 
-// End of batch: zero the V rows in T, write the h-degrees of the sources.
 template <int W>
-__global__ void __launch_bounds__(kBlock) k_end(BfsBufs b, const int32_t *__restrict__ src, int32_t ns,
-                                                int32_t *__restrict__ deg)
+__global__ void __launch_bounds__(kBlock) k_end(BfsBufs b, const int32_t *src, int32_t ns, int32_t *deg)
 {
-    const int lane = threadIdx.x & 31;
-    const int j = lane % W;
-    const int grp = lane / W;
-    constexpr int VPW = 32 / W;
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t warp = tid >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int32_t nt = b.ctl->t;
-    for (int64_t base = warp * VPW; base < nt; base += nwarps * VPW) {
-        const int64_t idx = base + grp;
-        if (idx < nt) b.V[(size_t)b.T[idx] * W + j] = 0;
-    }
-    if (tid < ns) {
-        deg[src[tid]] = b.cnt[tid];
-        b.cnt[tid] = 0;
-    }
+    dev_end<W>(b, src, ns, deg);
 }
 
 template <int W>

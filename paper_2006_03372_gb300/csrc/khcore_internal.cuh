@@ -159,4 +159,52 @@ cudaError_t launch_snapshot_inner(const PeelView &p, const int32_t *cls_h, int l
 
 int max_blocks_per_sm_bfs(int W);
 
+// ---- persistent decomposition (khcore_persist.cu) ---------------------------
+
+// Grid barrier state (zero before the launch); err = 1 after a timed-out wait.
+struct GridSync {
+    unsigned count;
+    unsigned gen;
+    int err;
+    int pad;
+};
+
+// Statistics the persistent kernel accumulates (zero before the launch).
+struct PersistStats {
+    long long rounds;
+    long long source_batches;
+    long long recomputed_total;
+    long long deleted_total;
+    long long affected_total;
+    long long level_steps;  // BFS level phases run
+    double level_bytes;     // their algorithmic bytes (4 n_b + 4 m_b + 16 W n_b each)
+};
+
+// Everything the persistent kernel works on (device pointers).
+struct PersistLaunch {
+    GraphView g;
+    uint32_t *alive;
+    int32_t *deg, *core, *rnd;
+    PeelView p;
+    PeelState *st;
+    BfsBufs b;
+    uint32_t *vis;
+    int32_t *A;
+    int32_t *aq[3];
+    int32_t *dcls;
+    int32_t *cls_src;
+    const int32_t *cls_h, *cls_size, *cls_off;  // [ncls]
+    int32_t *inner;
+    int32_t *dcount;
+    int32_t ncls, hmax, alpha;
+    GridSync *gs;
+    PersistStats *ps;
+    unsigned long long timeout_ns;  // limit of one barrier wait
+};
+
+// Cooperative launch of the whole decomposition; grid must not exceed
+// max_blocks_per_sm_persist(W) * SMs.
+cudaError_t launch_decompose_persist(int W, const PersistLaunch &L, int grid, cudaStream_t s);
+int max_blocks_per_sm_persist(int W);
+
 }  // namespace khc

@@ -1,0 +1,291 @@
+// khcore_persist.cuh — the whole decomposition in one cooperative launch.
+//
+// The host-driven path launches every phase of every round and waits for the
+// round's counts before planning the recompute; on graphs that need tens of
+// thousands of rounds that launch-and-wait cost dominates. Here one persistent
+// kernel (grid = every block that can be resident, launched cooperatively so
+// that all blocks run at once) steps through the same phases:
+//   initial h-degrees -> [level min -> set level -> peel set -> affected BFS
+//   -> recompute / outer-shell update] per round
+// separated by grid barriers. The decisions between phases (batch plans,
+// push or pull, the end of the loop) read device counters after a barrier,
+// so every block takes the same path. Small serial steps (resetting counters,
+// snapshots, statistics) run in the barrier itself, on the block that arrives
+// last, while every other block waits.
+//
+// Every barrier wait has a time limit: a block that waits longer sets an
+// error flag and leaves; every block checks the flag after each barrier and
+// returns, so a stuck barrier ends the launch with KHCORE_ETIMEOUT instead of
+// hanging the GPU.
+#pragma once
+
+#include "khcore_device.cuh"
+
+namespace khc {
+
+namespace {
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid barrier; serial() runs on one thread of the last block to arrive,
+// before any block is released. Returns false once any wait has timed out.
+template <class F>
+__device__ __forceinline__ bool grid_sync(GridSync *gs, unsigned long long timeout_ns, F serial)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = &gs->gen;
+        const unsigned g0 = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&gs->count, 1u);
+        if (arrived == gridDim.x - 1) {
+            __threadfence();
+            serial();
+            gs->count = 0;
+            __threadfence();
+            atomicAdd(&gs->gen, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (*vgen == g0) {
+                if (global_ns() - t0 > timeout_ns) {
+                    atomicExch(&gs->err, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = *((volatile int *)&gs->err) == 0;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+struct Nop {
+    __device__ void operator()() const {}
+};
+
+struct PersistArgs {
+    GraphView g;
+    uint32_t *alive;
+    int32_t *deg, *core, *rnd;
+    PeelView p;
+    PeelState *st;
+    BfsBufs b;
+    uint32_t *vis;       // affected-BFS visited bits
+    int32_t *A;          // affected vertices, class regions
+    int32_t *aq[3];      // affected-BFS frontier ring (slot 0 starts as the deleted set)
+    int32_t *dcls;       // deleted vertices, class regions
+    int32_t *cls_src;    // every vertex, class regions (initial pass)
+    const int32_t *cls_h, *cls_size, *cls_off;  // per class
+    int32_t *inner;      // per class: affected vertices closer than h
+    int32_t *dcount;     // per vertex: deleted vertices within h
+    int32_t ncls, hmax, alpha;
+    GridSync *gs;
+    PersistStats *ps;
+    unsigned long long timeout_ns;
+};
+
+// One batch of the multi-source BFS (sources src[0..ns), h levels), every
+// block taking part; phases separated by barriers. Returns false on timeout.
+template <int W>
+__device__ bool bfs_batch(const PersistArgs &a, const int32_t *src, int32_t ns, int32_t h, int32_t *rowcnt)
+{
+    BfsBufs b = a.b;
+    b.rowcnt = rowcnt;
+    LevelCtl *ctl = b.ctl;
+    // reset the level ring and place the sources (level 0)
+    if (!grid_sync(a.gs, a.timeout_ns, [&] {
+            for (int k = 0; k < 3; k++) {
+                ctl->q[k] = 0;
+                ctl->qh[k] = 0;
+                ctl->fe[k] = 0;
+            }
+            ctl->q[0] = ns;
+            ctl->t = ns;
+        }))
+        return false;
+    {
+        const int lane = threadIdx.x & 31;
+        for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < ns; i0 += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t i = i0 + threadIdx.x;  // block-uniform loop
+            unsigned long long d = 0;
+            int32_t s = -1;
+            if (i < ns) {
+                s = src[i];
+                d = (unsigned long long)(a.g.row_ptr[s + 1] - a.g.row_ptr[s]);
+                const int word = (int)(i >> 6);
+                const uint64_t bit = 1ull << (i & 63);
+                b.V[(size_t)s * W + word] = bit;     // V rows are zero between batches
+                b.F[0][(size_t)s * W + word] = bit;  // so are F rows
+                b.flag[0][s] = 1;
+                b.Q[0][i] = s;
+                b.T[i] = s;
+            }
+            warp_append(i < ns && d > (unsigned long long)kPushChunk, s, b.QH[0], &ctl->qh[0]);
+            const unsigned long long ws = warp_sum(d);
+            if (lane == 0 && ws) {
+                atomicAdd(&ctl->fe[0], ws);
+                atomicAdd(b.edges, ws);  // every source scans its own row
+            }
+        }
+    }
+    BfsTuning tune;
+    tune.alpha = a.alpha;
+    for (int lvl = 0; lvl < h; lvl++) {
+        if (!grid_sync(a.gs, a.timeout_ns, [&] {
+                a.ps->level_bytes += (double)(4.0 * a.st->alive + 4.0 * (double)a.st->m_alive + 16.0 * W * a.st->alive);
+                a.ps->level_steps++;
+            }))
+            return false;
+        tune.m_alive = *((volatile unsigned long long *)&a.st->m_alive);
+        if (lvl == h - 1)
+            dev_level<W, true>(a.g, a.alive, b, lvl, tune);
+        else
+            dev_level<W, false>(a.g, a.alive, b, lvl, tune);
+        if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return false;
+        if (lvl == h - 1)
+            dev_post<W, true>(a.g, b, lvl, tune);
+        else
+            dev_post<W, false>(a.g, b, lvl, tune);
+    }
+    if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return false;
+    dev_end<W>(b, src, ns, a.deg);
+    return true;
+}
+
+// h-degrees of src[0..ns) in batches of 64*W sources.
+template <int W>
+__device__ bool bfs_sources(const PersistArgs &a, const int32_t *src, int32_t ns, int32_t h, int32_t *rowcnt)
+{
+    constexpr int32_t S = 64 * W;
+    for (int32_t off = 0; off < ns; off += S) {
+        const int32_t cur = ns - off < S ? ns - off : S;
+        if (!bfs_batch<W>(a, src + off, cur, h, rowcnt)) return false;
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.ps->source_batches++;
+    }
+    return true;
+}
+
+template <int W>
+__global__ void __launch_bounds__(kBlock) k_decompose(PersistArgs a)
+{
+    // initial h-degrees, class by class
+    for (int32_t c = 0; c < a.ncls; c++)
+        if (!bfs_sources<W>(a, a.cls_src + a.cls_off[c], a.cls_size[c], a.cls_h[c], nullptr)) return;
+
+    for (;;) {
+        // level of every graph: k_g <- max(k_g, min alive h-degree)
+        if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
+        dev_min_alive_deg(a.g.n, a.alive, a.deg, a.p);
+        if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
+        dev_set_level(a.p, a.st);
+        // peel set D
+        if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
+        dev_peel_compact(a.g.n, a.g.row_ptr, a.alive, a.deg, a.p, a.st, a.core, a.rnd, a.vis, a.aq[0], a.dcls);
+        // affected set A: BFS from D through survivors; snapshot the per-class
+        // counts before the level that reaches distance h of each class
+        for (int lvl = 0; lvl < a.hmax; lvl++) {
+            if (!grid_sync(a.gs, a.timeout_ns, [&] {
+                    for (int32_t c = 0; c < a.p.ncls; c++)
+                        if (a.cls_h[c] == lvl + 1) a.inner[c] = a.p.nAc[c];
+                }))
+                return;
+            dev_affected_push(a.g, a.alive, lvl, a.aq[0], a.aq[1], a.aq[2], a.vis, a.p, a.st, a.A, lvl == a.hmax - 1);
+        }
+        if (!grid_sync(a.gs, a.timeout_ns, [&] {
+                int32_t s = 0;
+                for (int32_t c = 0; c < a.p.ncls; c++) s += a.p.nAc[c];
+                a.st->nA = s;
+                a.ps->rounds++;
+                a.ps->deleted_total += a.st->nD;
+                a.ps->affected_total += s;
+            }))
+            return;
+        const int32_t alive_left = *((volatile int32_t *)&a.st->alive);
+        if (alive_left == 0) break;
+        const bool single = *((volatile int32_t *)&a.st->nD) == 1;
+        // recompute the inner part of A; update the outer shell by counting
+        for (int32_t c = 0; c < a.ncls; c++) {
+            const int32_t na = *((volatile int32_t *)&a.p.nAc[c]);
+            int32_t ni = *((volatile int32_t *)&a.inner[c]);
+            ni = ni < na ? ni : na;
+            const int32_t nd = *((volatile int32_t *)&a.p.nDc[c]);
+            if (na == 0) continue;
+            int32_t *Ac = a.A + a.cls_off[c];
+            if (ni > 0 && !bfs_sources<W>(a, Ac, ni, a.cls_h[c], nullptr)) return;
+            if (blockIdx.x == 0 && threadIdx.x == 0) a.ps->recomputed_total += ni;
+            if (na > ni) {
+                if (!single && !bfs_sources<W>(a, a.dcls + a.cls_off[c], nd, a.cls_h[c], a.dcount)) return;
+                if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
+                dev_apply_dcount(Ac, ni, na, single ? nullptr : a.dcount, a.deg);
+            }
+        }
+        if (!grid_sync(a.gs, a.timeout_ns, [&] { a.st->round++; })) return;
+    }
+}
+
+}  // namespace
+
+// Per-W entry points, one translation unit each (khcore_persist_w*.cu).
+template <int W>
+cudaError_t persist_launch_w(const PersistLaunch &L, int grid, cudaStream_t s)
+{
+    PersistArgs a;
+    a.g = L.g;
+    a.alive = L.alive;
+    a.deg = L.deg;
+    a.core = L.core;
+    a.rnd = L.rnd;
+    a.p = L.p;
+    a.st = L.st;
+    a.b = L.b;
+    a.vis = L.vis;
+    a.A = L.A;
+    for (int k = 0; k < 3; k++) a.aq[k] = L.aq[k];
+    a.dcls = L.dcls;
+    a.cls_src = L.cls_src;
+    a.cls_h = L.cls_h;
+    a.cls_size = L.cls_size;
+    a.cls_off = L.cls_off;
+    a.inner = L.inner;
+    a.dcount = L.dcount;
+    a.ncls = L.ncls;
+    a.hmax = L.hmax;
+    a.alpha = L.alpha;
+    a.gs = L.gs;
+    a.ps = L.ps;
+    a.timeout_ns = L.timeout_ns;
+    void *args[] = {&a};
+    return cudaLaunchCooperativeKernel((const void *)k_decompose<W>, grid, kBlock, args, 0, s);
+}
+
+template <int W>
+int persist_occupancy_w()
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_decompose<W>, kBlock, 0) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+cudaError_t persist_launch_1(const PersistLaunch &L, int grid, cudaStream_t s);
+cudaError_t persist_launch_2(const PersistLaunch &L, int grid, cudaStream_t s);
+cudaError_t persist_launch_4(const PersistLaunch &L, int grid, cudaStream_t s);
+cudaError_t persist_launch_8(const PersistLaunch &L, int grid, cudaStream_t s);
+cudaError_t persist_launch_16(const PersistLaunch &L, int grid, cudaStream_t s);
+int persist_occupancy_1();
+int persist_occupancy_2();
+int persist_occupancy_4();
+int persist_occupancy_8();
+int persist_occupancy_16();
+
+}  // namespace khc

@@ -22,8 +22,8 @@ def kh():
     return kh
 
 
-def _run(kh, g, h, words=0, rounds=False):
-    with kh.KHCore.from_graph(g, words=words) as ctx:
+def _run(kh, g, h, words=0, loop=None):
+    with kh.KHCore.from_graph(g, words=words, loop=loop) as ctx:
         d = ctx.hdegrees(h)
         c, r, st = ctx.decompose_ex(h)
     return d, c, r, st
@@ -44,13 +44,14 @@ def test_fig1_example(kh, fig1):
 
 
 @pytest.mark.parametrize("h", [1, 2, 3, 4, 5])
-def test_small_graphs_all_words(kh, h):
+@pytest.mark.parametrize("loop", [0, 1])
+def test_small_graphs_all_words(kh, h, loop):
     for g in small_graphs(40 + h, 9, (2, 300)):
         want_d = oracle.hdegrees(g, h)
         want_c = oracle.peel(g, h)
         for w in WORDS:
             for alpha in [0, 16, 1 << 20]:
-                with kh.KHCore.from_graph(g, words=w, alpha=alpha) as ctx:
+                with kh.KHCore.from_graph(g, words=w, alpha=alpha, loop=loop) as ctx:
                     d = ctx.hdegrees(h)
                     c, r, st = ctx.decompose_ex(h)
                 assert (d == want_d).all(), (g.name, h, w, alpha)
@@ -60,11 +61,12 @@ def test_small_graphs_all_words(kh, h):
                     assert fails == 0
 
 
-def test_config1_er_h2_exact(kh):
+@pytest.mark.parametrize("loop", [0, 1])
+def test_config1_er_h2_exact(kh, loop):
     g = gg.config1_er()
     want = oracle.peel(g, 2)
     for w in [0, 1, 4, 16]:
-        d, c, r, st = _run(kh, g, 2, words=w)
+        d, c, r, st = _run(kh, g, 2, words=w, loop=loop)
         assert (d == oracle.hdegrees(g, 2)).all()
         assert (c == want).all()
         assert oracle.certificate(g, 2, c, r)[0] == 0
@@ -81,7 +83,7 @@ def test_ragged_batches_and_degree_classes(kh):
         want_c = oracle.peel(g, h) if h < 3 else None
         for w in [1, 8, 16]:
             for alpha in [0, 16, 1 << 20]:  # pull only, automatic, push wherever possible
-                with kh.KHCore.from_graph(g, words=w, alpha=alpha) as ctx:
+                with kh.KHCore.from_graph(g, words=w, alpha=alpha, loop=(w // 8) % 2) as ctx:
                     assert (ctx.hdegrees(h) == want_d).all(), (h, w, alpha)
                     if want_c is not None:
                         assert (ctx.decompose(h) == want_c).all(), (h, w, alpha)
@@ -172,8 +174,9 @@ def test_batch_matches_solo_oracle(kh):
     v_off, e_off, rp, col = kh.pack_graphs(graphs)
     ctx = kh.khcore_batch_create(v_off, e_off, rp, col)
     try:
-        for w in [1, 4, 16]:
+        for w, loop in [(1, 0), (4, 1), (16, 0)]:
             kh.khcore_set_words(ctx, w)
+            kh.khcore_set_round_loop(ctx, loop)
             core, rnd, st = kh.khcore_batch_decompose(ctx, np.array(hs, dtype=np.int32))
             for g, h, a, b in zip(graphs, hs, v_off[:-1], v_off[1:]):
                 assert (core[a:b] == oracle.peel(g, h)).all(), (g.name, h, w)
@@ -187,3 +190,17 @@ def test_batch_matches_solo_oracle(kh):
             assert (d[a:b] == oracle.hdegrees(g, 3)).all()
     finally:
         kh.khcore_destroy(ctx)
+
+
+def test_barrier_wait_limit_returns_etimeout_and_recovers(kh):
+    """A grid-barrier wait that runs out ends the persistent launch with
+    KHCORE_ETIMEOUT (no hang, no fault); the next call is exact again."""
+    g = gg.erdos_renyi_gnm(3000, 12000, 12)
+    want = oracle.peel(g, 2)
+    with kh.KHCore.from_graph(g) as ctx:
+        kh.khcore_set_wait_limit(ctx.ctx, 0)
+        with pytest.raises(kh.KHCoreError) as ei:
+            ctx.decompose(2)
+        assert ei.value.status == 4
+        kh.khcore_set_wait_limit(ctx.ctx, 10 ** 10)
+        assert (ctx.decompose(2) == want).all()
