@@ -63,7 +63,7 @@ typedef struct {
     int32_t h;                 /* h actually used: min(h, max(n-1, 1)) */
     int32_t rounds;            /* peel rounds (level-synchronous deletions) */
     int32_t k_max;             /* largest core index */
-    int32_t words_per_vertex;  /* W: 64-bit words per vertex per source batch */
+    int32_t words_per_vertex;  /* W of the initial h-degree pass (64*W sources per batch) */
     int64_t deleted_total;     /* sum over rounds of |D| (equals n) */
     int64_t affected_total;    /* sum over rounds of |A| (vertices recomputed) */
     int64_t source_batches;    /* multi-source BFS batches run, initial pass included */
@@ -189,6 +189,14 @@ int32_t khcore_num_graphs(const khcore_ctx *ctx);
 khcore_status khcore_set_words(khcore_ctx *ctx, int32_t words);
 
 /*
+ * khcore_set_round_words — W of the BFS batches of the peel rounds (the
+ * recompute of the affected vertices and the count from the deleted set),
+ * separately from the initial all-vertex pass (khcore_set_words). Same
+ * values; 0 = automatic (at most 4). Results do not depend on it.
+ */
+khcore_status khcore_set_round_words(khcore_ctx *ctx, int32_t words);
+
+/*
  * khcore_set_push_alpha — direction choice of the multi-source BFS: a level
  * expands in the push direction (frontier vertices scatter to neighbours)
  * when (sum of frontier degrees) * alpha < CSR entries of the alive graph,
@@ -271,6 +279,10 @@ khcore_status khcore_server_wait(khcore_server *srv, uint64_t ticket, int32_t *c
  * in use (each pointer may be NULL). */
 khcore_status khcore_server_stats(khcore_server *srv, int64_t *queued, int64_t *completed,
                                   int64_t *batches, size_t *bytes_in_use);
+
+/* Message of the last failed request returned by khcore_server_wait ("" if
+ * none); valid until the next khcore_server_wait. */
+const char *khcore_server_last_error(khcore_server *srv);
 
 /* Stop the workers after their current batch; queued requests are dropped. */
 void khcore_server_destroy(khcore_server *srv);

@@ -28,7 +28,7 @@ from ._build import build as _build_lib
 __all__ = [
     "KHCoreError", "khcore_create", "khcore_hdegrees", "khcore_decompose", "khcore_decompose_ex",
     "khcore_destroy", "khcore_last_error", "khcore_set_words", "khcore_set_profiling",
-    "khcore_set_push_alpha", "khcore_set_round_loop", "khcore_set_wait_limit",
+    "khcore_set_push_alpha", "khcore_set_round_loop", "khcore_set_wait_limit", "khcore_set_round_words",
     "khcore_status_string", "Stats",
     "KHCore", "library_path", "load_library", "khcore_batch_create", "khcore_batch_decompose", "pack_graphs",
     "khcore_hdegrees_of", "Server", "request_bytes",
@@ -96,6 +96,8 @@ def load_library(build_if_missing: bool = False):
         lib.khcore_status_string.restype = ctypes.c_char_p
         lib.khcore_set_words.argtypes = [P, i32]
         lib.khcore_set_words.restype = ctypes.c_int
+        lib.khcore_set_round_words.argtypes = [P, i32]
+        lib.khcore_set_round_words.restype = ctypes.c_int
         lib.khcore_set_push_alpha.argtypes = [P, i32]
         lib.khcore_set_push_alpha.restype = ctypes.c_int
         lib.khcore_set_round_loop.argtypes = [P, i32]
@@ -124,6 +126,8 @@ def load_library(build_if_missing: bool = False):
         lib.khcore_server_stats.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64),
                                             ctypes.POINTER(sz)]
         lib.khcore_server_stats.restype = ctypes.c_int
+        lib.khcore_server_last_error.argtypes = [P]
+        lib.khcore_server_last_error.restype = ctypes.c_char_p
         lib.khcore_server_destroy.argtypes = [P]
         lib.khcore_server_destroy.restype = None
         lib.khcore_num_graphs.argtypes = [P]
@@ -201,6 +205,11 @@ def khcore_status_string(status: int) -> str:
 def khcore_set_words(ctx, words: int) -> None:
     lib = load_library()
     _check(lib, ctx, lib.khcore_set_words(ctx, int(words)))
+
+
+def khcore_set_round_words(ctx, words: int) -> None:
+    lib = load_library()
+    _check(lib, ctx, lib.khcore_set_round_words(ctx, int(words)))
 
 
 def khcore_set_push_alpha(ctx, alpha: int) -> None:
@@ -361,7 +370,8 @@ class Server:
         if st != 0:
             if st == 4:
                 self._n[ticket] = n
-            raise KHCoreError(st, "khcore_server_wait failed")
+            msg = self.lib.khcore_server_last_error(self.h)
+            raise KHCoreError(st, "khcore_server_wait: " + (msg.decode() if msg else ""))
         return out[:n], lat.value
 
     def stats(self):

@@ -52,7 +52,8 @@ struct khcore_ctx {
     int32_t *nAc_host = nullptr;   // pinned mirror of nAc, inner, nDc (3 x G)
 
     // BFS buffers, sized for W_alloc words per vertex
-    int W_req = 0;  // 0 = automatic
+    int W_req = 0;   // 0 = automatic
+    int Wr_req = 0;  // W of the peel rounds, 0 = automatic
     int W_alloc = 0;
     uint64_t *V = nullptr, *F[2] = {nullptr, nullptr};
     uint8_t *flag[2] = {nullptr, nullptr};
@@ -210,23 +211,25 @@ bool validate_csr(int32_t n, const std::vector<int32_t> &rp, const std::vector<i
     return true;
 }
 
+// W of the all-vertex h-degree pass: the widest batch (1024 sources) amortises
+// the CSR scan of every level best; small graphs take the smallest W whose
+// batch holds every vertex.
 int auto_words(int32_t n)
 {
-    // 64*W sources per batch; keep one frontier array (n*W*8 bytes) near
-    // 32 MB so that the neighbour gathers stay in L2, with W in [4, 16]
-    // (W >= 4 makes each gather a whole 32-byte sector).
-    if (n <= 64) return 1;
-    if (n <= 128) return 2;
-    if (n <= 256) return 4;
-    int64_t w = (int64_t)(32ll << 20) / ((int64_t)n * 8);
-    int W = 4;
-    while (W < 16 && 2 * W <= w) W *= 2;
+    int W = 1;
+    while (W < 16 && 64 * W < n) W *= 2;
     return W;
 }
 
+// W of the peel rounds: their source sets (the affected vertices closer than
+// h to the deleted set) are usually small, and a narrow row keeps the level
+// kernels at two resident blocks per SM and 32/W edges per warp step in the
+// push direction.
+int auto_round_words(int32_t n) { return std::min(auto_words(n), 4); }
+
 khcore_status ensure_bfs(khcore_ctx *c, int W)
 {
-    if (c->W_alloc == W) return KHCORE_OK;
+    if (c->W_alloc >= W) return KHCORE_OK;  // rows of any narrower W fit the same arrays
     cudaFree(c->V);
     cudaFree(c->F[0]);
     cudaFree(c->F[1]);
@@ -524,12 +527,13 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         return KHCORE_OK;
     }
     const int W = c->W_req ? c->W_req : auto_words(c->n);
+    const int Wr = c->Wr_req ? c->Wr_req : (c->W_req ? c->W_req : auto_round_words(c->n));
     stt.words_per_vertex = W;
     khcore_status s;
-    if ((s = ensure_bfs(c, W)) != KHCORE_OK) return s;
+    if ((s = ensure_bfs(c, std::max(W, Wr))) != KHCORE_OK) return s;
     if ((s = clear_if_dirty(c)) != KHCORE_OK) return s;
     const GraphView g = c->view();
-    const int grid = bfs_grid(c, W);
+    const int grid = bfs_grid(c, Wr);
 
     PeelView pv;
     pv.G = G;
@@ -570,7 +574,13 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
     // the host vectors above must outlive the async copies
     CU(cudaStreamSynchronize(c->stream));
 
-    const int pgrid = c->round_loop == 0 ? c->sm_count * max_blocks_per_sm_persist(W) : 0;
+    // initial h-degrees, class by class
+    for (int32_t k = 0; k < ncls; k++)
+        if ((s = hdeg_sources(c, W, cls_h[k], c->cls_src + cls_off[k], (int32_t)cls_size[k], c->n, c->m, &stt)) !=
+            KHCORE_OK)
+            return s;
+
+    const int pgrid = c->round_loop == 0 ? c->sm_count * max_blocks_per_sm_persist(Wr) : 0;
     if (pgrid > 0) {
         // the whole decomposition in one cooperative launch
         PersistLaunch L;
@@ -613,7 +623,7 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         L.timeout_ns = c->wait_limit_ns;
         CU(cudaMemsetAsync(c->gs, 0, sizeof(GridSync), c->stream));
         CU(cudaMemsetAsync(c->pstats, 0, sizeof(PersistStats), c->stream));
-        CU(launch_decompose_persist(W, L, pgrid, c->stream));
+        CU(launch_decompose_persist(Wr, L, pgrid, c->stream));
         GridSync gsh;
         PersistStats psh;
         CU(cudaMemcpyAsync(&gsh, c->gs, sizeof gsh, cudaMemcpyDeviceToHost, c->stream));
@@ -637,11 +647,6 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         return finish_decompose(c, G, core_out, round_out, stats, stt, true);
     }
 
-    // initial h-degrees, class by class
-    for (int32_t k = 0; k < ncls; k++)
-        if ((s = hdeg_sources(c, W, cls_h[k], c->cls_src + cls_off[k], (int32_t)cls_size[k], c->n, c->m, &stt)) !=
-            KHCORE_OK)
-            return s;
 
     // KHCORE_TRACE=1 prints one line per peel round to stderr (tracing aid)
     const char *trace_env = getenv("KHCORE_TRACE");
@@ -692,14 +697,14 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
             const int32_t ni = std::min(c->nAc_host[G + k], na);
             const int32_t nd = c->nAc_host[2 * G + k];
             if (na == 0) continue;
-            if (ni > 0 && (s = hdeg_sources(c, W, cls_h[k], c->src + cls_off[k], ni, ps.alive, (int64_t)ps.m_alive,
+            if (ni > 0 && (s = hdeg_sources(c, Wr, cls_h[k], c->src + cls_off[k], ni, ps.alive, (int64_t)ps.m_alive,
                                             &stt)) != KHCORE_OK)
                 return s;
             stt.recomputed_total += ni;
             if (na > ni) {
                 const bool single = (ps.nD == 1);
                 if (!single &&
-                    (s = hdeg_sources(c, W, cls_h[k], c->dcls + cls_off[k], nd, ps.alive, (int64_t)ps.m_alive, &stt,
+                    (s = hdeg_sources(c, Wr, cls_h[k], c->dcls + cls_off[k], nd, ps.alive, (int64_t)ps.m_alive, &stt,
                                       c->dcount)) != KHCORE_OK)
                     return s;
                 CU(launch_apply_dcount(c->src + cls_off[k], ni, na, single ? nullptr : c->dcount, c->deg, c->stream));
@@ -859,6 +864,15 @@ khcore_status khcore_set_words(khcore_ctx *c, int32_t words)
     if (words != 0 && words != 1 && words != 2 && words != 4 && words != 8 && words != 16)
         return fail(c, KHCORE_EINVAL, "words must be 0, 1, 2, 4, 8 or 16 (got %d)", words);
     c->W_req = words;
+    return KHCORE_OK;
+}
+
+khcore_status khcore_set_round_words(khcore_ctx *c, int32_t words)
+{
+    if (!c) return KHCORE_EINVAL;
+    if (words != 0 && words != 1 && words != 2 && words != 4 && words != 8 && words != 16)
+        return fail(c, KHCORE_EINVAL, "words must be 0, 1, 2, 4, 8 or 16 (got %d)", words);
+    c->Wr_req = words;
     return KHCORE_OK;
 }
 

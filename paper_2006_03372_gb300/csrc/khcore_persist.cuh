@@ -5,8 +5,8 @@
 // thousands of rounds that launch-and-wait cost dominates. Here one persistent
 // kernel (grid = every block that can be resident, launched cooperatively so
 // that all blocks run at once) steps through the same phases:
-//   initial h-degrees -> [level min -> set level -> peel set -> affected BFS
-//   -> recompute / outer-shell update] per round
+//   [level min -> set level -> peel set -> affected BFS
+//   -> recompute / outer-shell update] per round, after the initial h-degrees
 // separated by grid barriers. The decisions between phases (batch plans,
 // push or pull, the end of the loop) read device counters after a barrier,
 // so every block takes the same path. Small serial steps (resetting counters,
@@ -176,10 +176,8 @@ __device__ bool bfs_sources(const PersistArgs &a, const int32_t *src, int32_t ns
 template <int W>
 __global__ void __launch_bounds__(kBlock) k_decompose(PersistArgs a)
 {
-    // initial h-degrees, class by class
-    for (int32_t c = 0; c < a.ncls; c++)
-        if (!bfs_sources<W>(a, a.cls_src + a.cls_off[c], a.cls_size[c], a.cls_h[c], nullptr)) return;
-
+    // the initial h-degrees are in deg already (computed by the per-phase
+    // kernels at the widest W); the rounds follow
     for (;;) {
         // level of every graph: k_g <- max(k_g, min alive h-degree)
         if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;

@@ -88,6 +88,9 @@ void run_batch(khcore_server *s, std::vector<Request *> &batch, cudaStream_t str
     khcore_status st = khcore_batch_create(G, v_off.data(), e_off.data(), rp.data(), col.empty() ? nullptr : col.data(),
                                            KHCORE_FLAG_TRUST_INPUT, stream, &ctx);
     std::string msg;
+    // host-driven rounds: the small kernels of concurrent batches interleave
+    // on the device, where a persistent kernel would hold every SM
+    if (st == KHCORE_OK) st = khcore_set_round_loop(ctx, 1);
     if (st == KHCORE_OK) {
         st = khcore_batch_decompose(ctx, h.data(), core.data(), nullptr, nullptr);
         if (st != KHCORE_OK) msg = khcore_last_error(ctx);
@@ -244,6 +247,13 @@ khcore_status khcore_server_stats(khcore_server *s, int64_t *queued, int64_t *co
 }
 
 size_t khcore_request_bytes(int32_t n, int64_t m) { return request_bytes(n, m); }
+
+const char *khcore_server_last_error(khcore_server *s)
+{
+    if (!s) return "";
+    std::lock_guard<std::mutex> lk(s->mu);
+    return s->err.c_str();
+}
 
 void khcore_server_destroy(khcore_server *s)
 {
