@@ -58,7 +58,7 @@ struct khcore_ctx {
     uint64_t *V = nullptr, *F[2] = {nullptr, nullptr};
     uint8_t *flag[2] = {nullptr, nullptr};
     int32_t *Q[3] = {nullptr, nullptr, nullptr};
-    int32_t *QH[3] = {nullptr, nullptr, nullptr};
+    int2 *I[3] = {nullptr, nullptr, nullptr};
     int32_t *T = nullptr;
     LevelCtl *ctl = nullptr;
     int32_t *cnt = nullptr;
@@ -300,7 +300,7 @@ khcore_status hdeg_sources(khcore_ctx *c, int W, int32_t h, const int32_t *src, 
     b.flag[1] = c->flag[1];
     for (int k = 0; k < 3; k++) {
         b.Q[k] = c->Q[k];
-        b.QH[k] = c->QH[k];
+        b.I[k] = c->I[k];
     }
     b.T = c->T;
     b.ctl = c->ctl;
@@ -406,7 +406,8 @@ khcore_status setup_ctx(khcore_ctx *c, const std::vector<int32_t> &rp, const std
     A(dev_alloc(&c->flag[1], nflag));
     for (int k = 0; k < 3; k++) {
         A(dev_alloc(&c->Q[k], (size_t)n));
-        A(dev_alloc(&c->QH[k], (size_t)n));
+        // push items: every frontier row in chunks of at least 8 entries
+        A(dev_alloc(&c->I[k], (size_t)n + (size_t)m / 8 + 1));
     }
     A(dev_alloc(&c->T, (size_t)n));
     A(dev_alloc(&c->ctl, 1));
@@ -598,7 +599,7 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         L.b.flag[1] = c->flag[1];
         for (int k = 0; k < 3; k++) {
             L.b.Q[k] = c->Q[k];
-            L.b.QH[k] = c->QH[k];
+            L.b.I[k] = c->I[k];
             L.aq[k] = c->Q[k];  // the affected-BFS ring reuses the BFS frontier lists
         }
         L.b.T = c->T;
@@ -770,7 +771,7 @@ void khcore_destroy(khcore_ctx *c)
     void *bufs[] = {c->row_ptr, c->col, c->classes, c->gid, c->kg, c->ming, c->hg, c->gcls, c->cls_off, c->nAc,
                     c->nDc, c->inner, c->clsh, c->dcls, c->dcount, c->cls_size, c->gs, c->pstats,
                     c->cls_src, c->alive, c->deg, c->core, c->rnd, c->src, c->vis, c->st, c->V, c->F[0], c->F[1],
-                    c->flag[0], c->flag[1], c->Q[0], c->Q[1], c->Q[2], c->QH[0], c->QH[1], c->QH[2], c->T, c->ctl,
+                    c->flag[0], c->flag[1], c->Q[0], c->Q[1], c->Q[2], c->I[0], c->I[1], c->I[2], c->T, c->ctl,
                     c->cnt, c->edges};
     for (void *p : bufs) cudaFree(p);
     for (cudaEvent_t e : c->tev) cudaEventDestroy(e);

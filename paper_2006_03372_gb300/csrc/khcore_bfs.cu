@@ -14,7 +14,7 @@ __global__ void k_seed(const int32_t *src, int32_t ns, BfsBufs b, const int32_t 
 }
 
 template <int W, bool LAST>
-__global__ void __launch_bounds__(kBlock) k_level(GraphView g, const uint32_t *alive, BfsBufs b, int lvl,
+__global__ void __launch_bounds__(kBlock, (W >= 8 ? 1 : 2)) k_level(GraphView g, const uint32_t *alive, BfsBufs b, int lvl,
                                                   BfsTuning tune)
 {
     dev_level<W, LAST>(g, alive, b, lvl, tune);

@@ -157,16 +157,37 @@ __device__ __forceinline__ bool use_push(const LevelCtl *ctl, int slot, BfsTunin
            (unsigned long long)ctl->fe[slot] * (unsigned long long)tune.alpha < tune.m_alive;
 }
 
-// Append y (already claimed in the next frontier) to Q, and to QH if heavy.
-// Whole warp calls; pred marks the lanes that append.
-__device__ __forceinline__ void append_frontier(bool pred, int32_t y, int32_t deg, const BfsBufs &b,
-                                                int nslot, Acc &acc)
+// Append y (already claimed in the next frontier) to Q, and its CSR row as
+// push work items of push_chunk(W) entries. Whole warp calls; pred marks the
+// lanes that append.
+template <int W>
+__device__ __forceinline__ void append_frontier(bool pred, int32_t y, int32_t deg, const BfsBufs &b, int nslot,
+                                                Acc &acc, const int32_t *rp)
 {
+    constexpr int C = push_chunk(W);
     warp_append(pred, y, pick3(b.Q, nslot), &b.ctl->q[nslot]);
-    warp_append(pred && deg > kPushChunk, y, pick3(b.QH, nslot), &b.ctl->qh[nslot]);
+    int32_t nch = pred ? (deg + C - 1) / C : 0;
+    // warp-wide exclusive prefix of the item counts, one atomic per warp
+    const int lane = threadIdx.x & 31;
+    int32_t incl = nch;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int32_t t = __shfl_up_sync(kFull, incl, off);
+        if (lane >= off) incl += t;
+    }
+    const int32_t total = __shfl_sync(kFull, incl, 31);
+    if (total) {
+        int32_t base = 0;
+        if (lane == 0) base = atomicAdd(&b.ctl->qi[nslot], total);
+        base = __shfl_sync(kFull, base, 0) + incl - nch;
+        if (nch) {
+            int2 *items = pick3(b.I, nslot);
+            const int32_t e0 = rp[y];
+            for (int32_t k = 0; k < nch; k++) items[base + k] = make_int2(y, e0 + k * C);
+        }
+    }
     if (pred) acc.fe += (unsigned long long)deg;
 }
-
 
 // OR the W words of frontier row x into a.
 template <int W>
@@ -241,7 +262,7 @@ __device__ __forceinline__ void dev_seed(const int32_t *src, int32_t ns, BfsBufs
     if (i == 0) {
         for (int k = 0; k < 3; k++) {
             b.ctl->q[k] = 0;
-            b.ctl->qh[k] = 0;
+            b.ctl->qi[k] = 0;
             b.ctl->fe[k] = 0;
         }
         b.ctl->t = 0;
@@ -258,15 +279,14 @@ __device__ __forceinline__ void dev_seed(const int32_t *src, int32_t ns, BfsBufs
         b.V[(size_t)s * W + word] = bit;  // V(s) is zero between batches
         b.F[0][(size_t)s * W + word] = bit;  // F rows are zero between batches
         b.flag[0][s] = 1;
-        b.Q[0][i] = s;
         b.T[i] = s;
     }
-    warp_append(i < ns && d > (unsigned long long)kPushChunk, s, b.QH[0], &b.ctl->qh[0]);
+    Acc dummy{0, 0};
+    append_frontier<W>(i < ns, s, (int32_t)d, b, 0, dummy, rp);  // Q[0] and the level-0 push items
     const unsigned long long ws = warp_sum(d);
     if ((i & 31) == 0 && ws) atomicAdd(&s_fe, ws);
     __syncthreads();
     if (i == 0) {
-        b.ctl->q[0] = ns;
         b.ctl->t = ns;
         b.ctl->fe[0] = s_fe;
         if (s_fe) atomicAdd(b.edges, s_fe);  // every source scans its own row
@@ -280,7 +300,8 @@ __device__ __forceinline__ void dev_seed(const int32_t *src, int32_t ns, BfsBufs
 template <int W, int G>
 __device__ __forceinline__ void finish_vertex(bool act, int32_t y, int32_t dy, uint64_t nw, uint64_t v, int gi,
                                               int grp, uint64_t *V, uint64_t *Fn,
-                                              uint8_t *fln, const BfsBufs &b, int nslot, Acc &acc)
+                                              uint8_t *fln, const BfsBufs &b, int nslot, Acc &acc,
+                                              const int32_t *rp)
 {
     const unsigned gmask = (G == 32) ? kFull : ((1u << G) - 1u);
     const unsigned any = __ballot_sync(kFull, nw != 0);
@@ -294,7 +315,7 @@ __device__ __forceinline__ void finish_vertex(bool act, int32_t y, int32_t dy, u
     }
     const bool lead = act && gany && gi == 0;
     if (lead) fln[y] = 1;
-    append_frontier(lead, y, dy, b, nslot, acc);
+    append_frontier<W>(lead, y, dy, b, nslot, acc, rp);
     warp_append(lead && !gv, y, b.T, &b.ctl->t);
 }
 
@@ -342,7 +363,7 @@ __device__ __forceinline__ void pull_groups(const int32_t *list, int32_t count, 
             for (int off = 1; off < G; off <<= 1) rc += __shfl_xor_sync(kFull, rc, off);
             if (act && gi == 0 && rc) atomicAdd(&b.rowcnt[y], rc);
         }
-        if (!LAST) finish_vertex<W, G>(act, y, dy, nw, v, gi, grp, V, Fn, fln, b, nslot, acc);
+        if (!LAST) finish_vertex<W, G>(act, y, dy, nw, v, gi, grp, V, Fn, fln, b, nslot, acc, rp);
     }
 }
 
@@ -387,10 +408,9 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
         const int slot = lane / W;
         const int grp = slot;
         const unsigned gmask = (1u << W) - 1u;
-        const int32_t nq = b.ctl->q[cslot];
-        const int32_t nqh = b.ctl->qh[cslot];
-        const int32_t *Qc = pick3(b.Q, cslot);
-        const int32_t *QHc = pick3(b.QH, cslot);
+        constexpr int C = push_chunk(W);
+        const int32_t ni = b.ctl->qi[cslot];
+        const int2 *Ic = pick3(b.I, cslot);
         // one edge of the expansion: y = col[e] gets fx & ~V(y)
         auto edge = [&](int32_t e, int32_t e1, uint64_t fx) {
             int32_t y = -1;
@@ -417,23 +437,16 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
                 claimed = flag_claim(fln, y);
                 dy = rp[y + 1] - rp[y];
             }
-            append_frontier(claimed, y, dy, b, nslot, acc);
+            append_frontier<W>(claimed, y, dy, b, nslot, acc, rp);
         };
-        // light frontier vertices: one warp each
-        for (int64_t i = warp; i < nq; i += nwarps) {
-            const int32_t x = Qc[i];
-            const int32_t e0 = rp[x], e1 = rp[x + 1];
-            if (e1 - e0 > kPushChunk) continue;  // warp-uniform; handled below
+        // work items: up to C entries of one frontier row each, one warp per item
+        for (int64_t it = warp; it < ni; it += nwarps) {  // warp-uniform
+            const int2 item = Ic[it];
+            const int32_t x = item.x;
+            const int32_t rend = rp[x + 1];
+            const int32_t e1 = item.y + C < rend ? item.y + C : rend;
             const uint64_t fx = Fc[(size_t)x * W + j];
-            for (int32_t eb = e0; eb < e1; eb += SLOTS) edge(eb + slot, e1, fx);
-        }
-        // heavy frontier vertices: every warp of the grid takes a share
-        for (int32_t k = 0; k < nqh; k++) {
-            const int32_t x = QHc[k];
-            const int32_t e1 = rp[x + 1];
-            const uint64_t fx = Fc[(size_t)x * W + j];
-            for (int64_t eb = rp[x] + warp * SLOTS; eb < e1; eb += nwarps * SLOTS)
-                edge((int32_t)eb + slot, e1, fx);
+            for (int32_t eb = item.y; eb < e1; eb += SLOTS) edge(eb + slot, e1, fx);
         }
     } else {
         // ---------------- pull: every alive vertex gathers its neighbours ----
@@ -479,7 +492,7 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
                         for (int off = 1; off < 32; off <<= 1) rc += __shfl_xor_sync(kFull, rc, off);
                         if (act && lane == 0 && rc) atomicAdd(&b.rowcnt[y], rc);
                     }
-                    if (!LAST) finish_vertex<W, 32>(act, y, e1 - e0, nw, v, lane, 0, V, Fn, fln, b, nslot, acc);
+                    if (!LAST) finish_vertex<W, 32>(act, y, e1 - e0, nw, v, lane, 0, V, Fn, fln, b, nslot, acc, rp);
                 }
                 __syncthreads();
             }
@@ -523,7 +536,7 @@ __device__ __forceinline__ void dev_post(GraphView g, BfsBufs b, int lvl, BfsTun
 
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         b.ctl->q[oslot] = 0;
-        b.ctl->qh[oslot] = 0;
+        b.ctl->qi[oslot] = 0;
         b.ctl->fe[oslot] = 0;
     }
     const int32_t nq = b.ctl->q[cslot];

@@ -32,15 +32,16 @@ struct GraphView {
 // (l+1)%3, and slot (l+2)%3 is reset by the level's post kernel.
 struct LevelCtl {
     int32_t q[3];                // |Q| per slot: frontier vertex lists
-    int32_t qh[3];               // |QH| per slot: frontier vertices with deg > kPushChunk
+    int32_t qi[3];               // |I| per slot: push work items of the frontier
     unsigned long long fe[3];    // sum of CSR degrees over Q (direction choice)
     int32_t t;                   // |T|: vertices whose V row is nonzero
     int32_t pad;
 };
 
-// A frontier vertex with more CSR entries than this is expanded by every
-// warp of the grid in the push direction (hub splitting).
-constexpr int kPushChunk = 256;
+// Push work items: a frontier vertex's CSR row is cut into chunks of
+// push_chunk(W) = 4 * (32/W) entries (four warp steps), so that a hub's
+// edges spread over many warps. Item = (vertex, first entry).
+__host__ __device__ constexpr int push_chunk(int W) { return 4 * (32 / W); }
 
 // Multi-source BFS state for one batch of 64*W sources. Vertex-major: the W
 // words of vertex y are V[y*W .. y*W+W-1]; bit b of word j is source 64*j+b
@@ -50,7 +51,8 @@ constexpr int kPushChunk = 256;
 //   F[2]     frontier words of the current / next level; a row is nonzero
 //            only while its vertex is in that level's list Q
 //   flag[2]  one byte per vertex: 1 iff the vertex is in that frontier
-//   Q[3], QH[3], T  frontier lists (ring of three) and touched-row list
+//   Q[3], I[3], T   frontier lists and their push work items (ring of three),
+//                   touched-row list
 //   ctl      list lengths and frontier degree sums
 //   cnt      [64*W] per-source count of newly reached vertices; zero between
 //            batches
@@ -63,7 +65,7 @@ struct BfsBufs {
     uint64_t *F[2];
     uint8_t *flag[2];
     int32_t *Q[3];
-    int32_t *QH[3];
+    int2 *I[3];
     int32_t *T;
     LevelCtl *ctl;
     int32_t *cnt;

@@ -104,10 +104,9 @@ __device__ bool bfs_batch(const PersistArgs &a, const int32_t *src, int32_t ns, 
     if (!grid_sync(a.gs, a.timeout_ns, [&] {
             for (int k = 0; k < 3; k++) {
                 ctl->q[k] = 0;
-                ctl->qh[k] = 0;
+                ctl->qi[k] = 0;
                 ctl->fe[k] = 0;
             }
-            ctl->q[0] = ns;
             ctl->t = ns;
         }))
         return false;
@@ -125,11 +124,11 @@ __device__ bool bfs_batch(const PersistArgs &a, const int32_t *src, int32_t ns, 
                 b.V[(size_t)s * W + word] = bit;     // V rows are zero between batches
                 b.F[0][(size_t)s * W + word] = bit;  // so are F rows
                 b.flag[0][s] = 1;
-                b.Q[0][i] = s;
                 b.T[i] = s;
             }
-            warp_append(i < ns && d > (unsigned long long)kPushChunk, s, b.QH[0], &ctl->qh[0]);
-            const unsigned long long ws = warp_sum(d);
+            Acc acc0{0, 0};
+            append_frontier<W>(i < ns, s, (int32_t)d, b, 0, acc0, a.g.row_ptr);  // Q[0] and level-0 push items
+            const unsigned long long ws = warp_sum(acc0.fe);
             if (lane == 0 && ws) {
                 atomicAdd(&ctl->fe[0], ws);
                 atomicAdd(b.edges, ws);  // every source scans its own row
@@ -174,7 +173,7 @@ __device__ bool bfs_sources(const PersistArgs &a, const int32_t *src, int32_t ns
 }
 
 template <int W>
-__global__ void __launch_bounds__(kBlock) k_decompose(PersistArgs a)
+__global__ void __launch_bounds__(kBlock, (W <= 4 ? 2 : 1)) k_decompose(PersistArgs a)
 {
     // the initial h-degrees are in deg already (computed by the per-phase
     // kernels at the widest W); the rounds follow
