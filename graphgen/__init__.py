@@ -402,3 +402,35 @@ CONFIGS = {
 def config_graph(name: str) -> Graph:
     make, _ = CONFIGS[name]
     return cached(name, make)
+
+
+def config4_packed(count: int = 1024, first: int = None):
+    """The batching workload packed for khcore_batch_create: (graphs spec,
+    v_off, e_off, row_ptr_local, col_local, h). first=k keeps graphs 0..k-1.
+    Cached on disk (generation of all 1024 graphs takes a minute)."""
+    import os
+    spec = config4_spec(count)
+    k = count if first is None else min(first, count)
+    path = os.path.join(cache_dir(), f"batch{count}_first{k}.npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        return spec, z["v_off"], z["e_off"], z["rp"], z["col"], z["h"]
+    gs = [batch_graph(spec, i) for i in range(k)]
+    ns = np.array([g.n for g in gs], dtype=np.int64)
+    ms = np.array([len(g.col) for g in gs], dtype=np.int64)
+    v_off = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
+    e_off = np.concatenate([[0], np.cumsum(ms)]).astype(np.int64)
+    rp = np.concatenate([g.row_ptr for g in gs]).astype(np.int32)
+    col = np.concatenate([g.col for g in gs]).astype(np.int32)
+    h = spec.hs[:k].astype(np.int32)
+    tmp = path + f".tmp{os.getpid()}.npz"
+    np.savez(tmp, v_off=v_off, e_off=e_off, rp=rp, col=col, h=h)
+    os.replace(tmp, path)
+    return spec, v_off, e_off, rp, col, h
+
+
+def unpack(v_off, e_off, rp, col, i) -> Graph:
+    """Graph i of a packed batch."""
+    a, b = int(v_off[i]), int(v_off[i + 1])
+    ea, eb = int(e_off[i]), int(e_off[i + 1])
+    return Graph(b - a, rp[a + i:b + i + 1].copy(), col[ea:eb].copy(), f"batch{i}")

@@ -52,7 +52,8 @@ class Stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("device_ms", ctypes.c_double),
                 ("edges_traversed", ctypes.c_int64), ("level_launches", ctypes.c_int64),
                 ("level_ms", ctypes.c_double), ("level_bytes", ctypes.c_double),
-                ("recomputed_total", ctypes.c_int64)]
+                ("recomputed_total", ctypes.c_int64), ("init_ms", ctypes.c_double),
+                ("round_ms", ctypes.c_double), ("round_bytes", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -71,7 +71,7 @@ struct khcore_ctx {
     GridSync *gs = nullptr;
     PersistStats *pstats = nullptr;
 
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_init = nullptr;
 
     // profiling: an event pair around every BFS level launch
     bool profiling = false;
@@ -322,7 +322,7 @@ khcore_status hdeg_sources(khcore_ctx *c, int W, int32_t h, const int32_t *src, 
                          stt ? &stt->kernel_launches : nullptr, c->profiling ? &c->timer : nullptr));
         if (stt) {
             stt->source_batches++;
-            if (c->profiling) stt->level_bytes += (double)h * (4.0 * n_b + 4.0 * m_b + 16.0 * W * n_b);
+            stt->level_bytes += (double)h * (4.0 * n_b + 4.0 * m_b + 16.0 * W * n_b);
         }
     }
     return KHCORE_OK;
@@ -432,6 +432,7 @@ khcore_status setup_ctx(khcore_ctx *c, const std::vector<int32_t> &rp, const std
     if (e == cudaSuccess && n) e = cudaMemsetAsync(c->dcount, 0, sizeof(int32_t) * (size_t)n, c->stream);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev_init);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->row_ptr, rp.data(), ((size_t)n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice,
                             c->stream);
@@ -463,20 +464,24 @@ khcore_status finish_decompose(khcore_ctx *c, int32_t G, int32_t *core_out, int3
     CU(cudaMemcpyAsync(&edges, c->edges, sizeof edges, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaMemcpyAsync(kg.data(), c->kg, sizeof(int32_t) * G, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
-    float ms = 0.f;
+    float ms = 0.f, ms_init = 0.f;
     CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    CU(cudaEventElapsedTime(&ms_init, c->ev0, c->ev_init));
     stt.device_ms = ms;
+    stt.init_ms = ms_init;
+    stt.round_ms = ms - ms_init;
     stt.edges_traversed = (int64_t)edges;
     stt.k_max = *std::max_element(kg.begin(), kg.end());
     if (persistent) {
-        stt.level_ms = c->profiling ? ms : 0.0;
+        if ((s = flush_timer(c)) != KHCORE_OK) return s;  // the initial pass's level launches
+        stt.level_ms = c->level_ms;
+        stt.level_launches = c->level_launches;
     } else {
         if ((s = flush_timer(c)) != KHCORE_OK) return s;
         stt.level_ms = c->level_ms;
         stt.level_launches = c->level_launches;
     }
     if (!c->profiling) {
-        stt.level_bytes = 0;
         stt.level_ms = 0;
         stt.level_launches = 0;
     }
@@ -581,6 +586,8 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
             KHCORE_OK)
             return s;
 
+    CU(cudaEventRecord(c->ev_init, c->stream));
+    const double init_bytes = stt.level_bytes;
     const int pgrid = c->round_loop == 0 ? c->sm_count * max_blocks_per_sm_persist(Wr) : 0;
     if (pgrid > 0) {
         // the whole decomposition in one cooperative launch
@@ -641,10 +648,7 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         stt.recomputed_total += psh.recomputed_total;
         stt.deleted_total += psh.deleted_total;
         stt.affected_total += psh.affected_total;
-        if (c->profiling) {
-            stt.level_bytes = psh.level_bytes;
-            stt.level_launches = psh.level_steps;
-        }
+        stt.round_bytes = psh.level_bytes;
         return finish_decompose(c, G, core_out, round_out, stats, stt, true);
     }
 
@@ -717,6 +721,7 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         CU(cudaMemcpyAsync(&c->st->round, &c->st_host->round, sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
     }
     stt.rounds = round;
+    stt.round_bytes = stt.level_bytes - init_bytes;
     return finish_decompose(c, G, core_out, round_out, stats, stt, false);
 }
 
@@ -779,6 +784,7 @@ void khcore_destroy(khcore_ctx *c)
     if (c->nAc_host) cudaFreeHost(c->nAc_host);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->ev_init) cudaEventDestroy(c->ev_init);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     (void)cudaGetLastError();
     delete c;
