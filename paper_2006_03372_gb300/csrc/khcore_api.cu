@@ -441,7 +441,7 @@ khcore_status setup_ctx(khcore_ctx *c, const std::vector<int32_t> &rp, const std
     if (e == cudaSuccess && n)
         e = cudaMemcpyAsync(c->classes, classes.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice,
                             c->stream);
-    if (e == cudaSuccess && gid_host && n)
+    if (e == cudaSuccess && gid_host && n && c->gid)  // one graph needs no graph ids
         e = cudaMemcpyAsync(c->gid, gid_host->data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->flag[0], 0, nflag, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->flag[1], 0, nflag, c->stream);
