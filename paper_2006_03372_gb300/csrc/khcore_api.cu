@@ -42,6 +42,7 @@ struct khcore_ctx {
     int32_t *cls_src = nullptr;                  // [n] vertices grouped by h-class
     int32_t *dcls = nullptr;                     // [n] deleted vertices grouped by h-class (per round)
     int32_t *dcount = nullptr;                   // [n] deleted vertices within h (outer-shell update)
+    int32_t *comb = nullptr;                     // [n] round source list: inner vertices, then deleted ones
 
     // peel state (device)
     uint32_t *alive = nullptr;
@@ -288,8 +289,9 @@ khcore_status flush_timer(khcore_ctx *c)
 // h-degrees of the sources src[0..ns) in G[alive], in batches of 64*W.
 // n_b / m_b: alive rows and their CSR entries (direction choice and
 // algorithmic bytes).
+// rowcnt (nullable): row counts of the sources at list positions >= row_first.
 khcore_status hdeg_sources(khcore_ctx *c, int W, int32_t h, const int32_t *src, int32_t ns, int64_t n_b,
-                           int64_t m_b, khcore_stats *stt, int32_t *rowcnt = nullptr)
+                           int64_t m_b, khcore_stats *stt, int32_t *rowcnt = nullptr, int32_t row_first = 0)
 {
     const GraphView g = c->view();
     BfsBufs b;
@@ -307,6 +309,7 @@ khcore_status hdeg_sources(khcore_ctx *c, int W, int32_t h, const int32_t *src, 
     b.cnt = c->cnt;
     b.edges = c->edges;
     b.rowcnt = rowcnt;
+    b.row_first = 0;
     BfsTuning tune;
     tune.alpha = c->push_alpha;
     tune.m_alive = (unsigned long long)m_b;
@@ -314,6 +317,7 @@ khcore_status hdeg_sources(khcore_ctx *c, int W, int32_t h, const int32_t *src, 
     const int grid = bfs_grid(c, W);
     for (int32_t off = 0; off < ns; off += S) {
         const int32_t cur = std::min(S, ns - off);
+        b.row_first = std::max(0, row_first - off);
         if (c->profiling && c->timer.used + h > c->timer.cap) {
             khcore_status s = flush_timer(c);
             if (s != KHCORE_OK) return s;
@@ -422,6 +426,7 @@ khcore_status setup_ctx(khcore_ctx *c, const std::vector<int32_t> &rp, const std
     A(dev_alloc(&c->clsh, (size_t)c->G));
     A(dev_alloc(&c->dcls, (size_t)n));
     A(dev_alloc(&c->dcount, (size_t)n));
+    A(dev_alloc(&c->comb, (size_t)n));
     A(dev_alloc(&c->cls_size, (size_t)c->G));
     A(dev_alloc(&c->gs, 1));
     A(dev_alloc(&c->pstats, 1));
@@ -623,6 +628,7 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         L.cls_off = c->cls_off;
         L.inner = c->inner;
         L.dcount = c->dcount;
+        L.comb = c->comb;
         L.ncls = ncls;
         L.hmax = hmax;
         L.alpha = c->push_alpha;
@@ -702,18 +708,21 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
             const int32_t ni = std::min(c->nAc_host[G + k], na);
             const int32_t nd = c->nAc_host[2 * G + k];
             if (na == 0) continue;
-            if (ni > 0 && (s = hdeg_sources(c, Wr, cls_h[k], c->src + cls_off[k], ni, ps.alive, (int64_t)ps.m_alive,
-                                            &stt)) != KHCORE_OK)
-                return s;
+            const bool single = (ps.nD == 1);  // the outer shell loses exactly 1
+            const bool count_d = na > ni && !single;
+            // one source list: the inner vertices (their h-degrees) and, after
+            // them, the deleted vertices (row counts on the outer shell)
+            const int32_t total = ni + (count_d ? nd : 0);
+            if (total > 0) {
+                CU(launch_concat(c->comb, c->src + cls_off[k], ni, c->dcls + cls_off[k], count_d ? nd : 0, c->stream));
+                if ((s = hdeg_sources(c, Wr, cls_h[k], c->comb, total, ps.alive, (int64_t)ps.m_alive, &stt,
+                                      count_d ? c->dcount : nullptr, ni)) != KHCORE_OK)
+                    return s;
+            }
             stt.recomputed_total += ni;
             if (na > ni) {
-                const bool single = (ps.nD == 1);
-                if (!single &&
-                    (s = hdeg_sources(c, Wr, cls_h[k], c->dcls + cls_off[k], nd, ps.alive, (int64_t)ps.m_alive, &stt,
-                                      c->dcount)) != KHCORE_OK)
-                    return s;
                 CU(launch_apply_dcount(c->src + cls_off[k], ni, na, single ? nullptr : c->dcount, c->deg, c->stream));
-                stt.kernel_launches++;
+                stt.kernel_launches += 2;
             }
         }
         // advance the device-side round counter
@@ -774,7 +783,7 @@ void khcore_destroy(khcore_ctx *c)
     cudaSetDevice(c->device);
     if (c->stream && !c->failed) cudaStreamSynchronize(c->stream);
     void *bufs[] = {c->row_ptr, c->col, c->classes, c->gid, c->kg, c->ming, c->hg, c->gcls, c->cls_off, c->nAc,
-                    c->nDc, c->inner, c->clsh, c->dcls, c->dcount, c->cls_size, c->gs, c->pstats,
+                    c->nDc, c->inner, c->clsh, c->dcls, c->dcount, c->comb, c->cls_size, c->gs, c->pstats,
                     c->cls_src, c->alive, c->deg, c->core, c->rnd, c->src, c->vis, c->st, c->V, c->F[0], c->F[1],
                     c->flag[0], c->flag[1], c->Q[0], c->Q[1], c->Q[2], c->I[0], c->I[1], c->I[2], c->T, c->ctl,
                     c->cnt, c->edges};

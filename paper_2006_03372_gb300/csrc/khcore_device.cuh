@@ -138,6 +138,16 @@ __device__ __forceinline__ void swar_step(Swar &s, uint64_t w, int32_t *cnt_s)
     if (++s.n == 255) swar_flush<W>(s, cnt_s);
 }
 
+// Bits of word j that stand for row-counted sources (batch positions >=
+// row_first).
+__device__ __forceinline__ uint64_t row_mask(int j, int32_t row_first)
+{
+    const int32_t lo = 64 * j;
+    if (row_first <= lo) return ~0ull;
+    if (row_first >= lo + 64) return 0ull;
+    return ~0ull << (row_first - lo);
+}
+
 // Per-thread accumulators flushed once at the end of a level kernel.
 struct Acc {
     unsigned long long scanned;  // plain-BFS-equivalent CSR entries
@@ -358,7 +368,7 @@ __device__ __forceinline__ void pull_groups(const int32_t *list, int32_t count, 
         }
         swar_step<W>(sw, nw, cnt_s);
         if (b.rowcnt) {  // uniform
-            int32_t rc = __popcll(nw);
+            int32_t rc = __popcll(nw & row_mask(gi, b.row_first));
 #pragma unroll
             for (int off = 1; off < G; off <<= 1) rc += __shfl_xor_sync(kFull, rc, off);
             if (act && gi == 0 && rc) atomicAdd(&b.rowcnt[y], rc);
@@ -424,7 +434,10 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
                             atomicOr(reinterpret_cast<unsigned long long *>(&Fn[(size_t)y * W + j]),
                                      (unsigned long long)nbits);
                         fresh = nbits & ~(uint64_t)old;
-                        if (b.rowcnt && fresh) atomicAdd(&b.rowcnt[y], __popcll(fresh));
+                        if (b.rowcnt) {
+                            const uint64_t rf = fresh & row_mask(j, b.row_first);
+                            if (rf) atomicAdd(&b.rowcnt[y], __popcll(rf));
+                        }
                     }
                 }
             }
@@ -487,7 +500,7 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
                     }
                     swar_step<W>(sw, nw, cnt_s);
                     if (b.rowcnt) {
-                        int32_t rc = __popcll(nw);
+                        int32_t rc = __popcll(nw & row_mask(lane, b.row_first));
 #pragma unroll
                         for (int off = 1; off < 32; off <<= 1) rc += __shfl_xor_sync(kFull, rc, off);
                         if (act && lane == 0 && rc) atomicAdd(&b.rowcnt[y], rc);
@@ -810,6 +823,13 @@ __device__ __forceinline__ void dev_apply_dcount(const int32_t *list, int32_t in
         if (i >= inner) deg[u] -= dcount ? dcount[u] : 1;
         if (dcount) dcount[u] = 0;
     }
+}
+
+__device__ __forceinline__ void dev_concat(int32_t *dst, const int32_t *a, int32_t na, const int32_t *b, int32_t nb)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)na + nb;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = i < na ? a[i] : b[i - na];
 }
 
 __device__ __forceinline__ void dev_snapshot_inner(PeelView p, const int32_t *cls_h, int lvl, int32_t *inner)

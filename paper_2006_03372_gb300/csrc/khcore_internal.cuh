@@ -59,7 +59,8 @@ __host__ __device__ constexpr int push_chunk(int W) { return 4 * (32 / W); }
 //   edges    plain-BFS-equivalent CSR entries scanned: sum over sources s and
 //            vertices x with dist(s, x) < h of deg(x) (for GTEPS reporting)
 //   rowcnt   optional [n]: when set, rowcnt[y] += number of batch sources
-//            that reach y at distance 1..h (row counts, the transpose of cnt)
+//            at bit position >= row_first that reach y at distance 1..h
+//            (row counts, the transpose of cnt)
 struct BfsBufs {
     uint64_t *V;
     uint64_t *F[2];
@@ -71,6 +72,7 @@ struct BfsBufs {
     int32_t *cnt;
     unsigned long long *edges;
     int32_t *rowcnt;
+    int32_t row_first;
 };
 
 // Direction choice of one level: push when (sum of frontier degrees) * alpha
@@ -153,6 +155,8 @@ cudaError_t launch_apply_dcount(const int32_t *list, int32_t inner, int32_t tota
 cudaError_t launch_affected_level(const GraphView &g, const uint32_t *alive, int lvl, int32_t *const aq[3],
                                   uint32_t *vis, const PeelView &p, PeelState *st, int32_t *A, int last, int grid,
                                   cudaStream_t s);
+// dst = a[0..na) followed by b[0..nb).
+cudaError_t launch_concat(int32_t *dst, const int32_t *a, int32_t na, const int32_t *b, int32_t nb, cudaStream_t s);
 // st->nA = sum of p.nAc.
 cudaError_t launch_sum_classes(const PeelView &p, PeelState *st, cudaStream_t s);
 // Before affected-BFS level lvl: inner[c] = p.nAc[c] for every class whose
@@ -198,6 +202,7 @@ struct PersistLaunch {
     const int32_t *cls_h, *cls_size, *cls_off;  // [ncls]
     int32_t *inner;
     int32_t *dcount;
+    int32_t *comb;  // [n] round source list
     int32_t ncls, hmax, alpha;
     GridSync *gs;
     PersistStats *ps;

@@ -36,6 +36,10 @@ __global__ void k_snapshot_inner(PeelView p, const int32_t *cls_h, int lvl, int3
     dev_snapshot_inner(p, cls_h, lvl, inner);
 }
 __global__ void k_sum_classes(PeelView p, PeelState *st) { dev_sum_classes(p, st); }
+__global__ void k_concat(int32_t *dst, const int32_t *a, int32_t na, const int32_t *b, int32_t nb)
+{
+    dev_concat(dst, a, na, b, nb);
+}
 
 }  // namespace
 
@@ -98,6 +102,15 @@ cudaError_t launch_affected_level(const GraphView &g, const uint32_t *alive, int
 cudaError_t launch_snapshot_inner(const PeelView &p, const int32_t *cls_h, int lvl, int32_t *inner, cudaStream_t s)
 {
     k_snapshot_inner<<<1, 256, 0, s>>>(p, cls_h, lvl, inner);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_concat(int32_t *dst, const int32_t *a, int32_t na, const int32_t *b, int32_t nb, cudaStream_t s)
+{
+    const int64_t t = (int64_t)na + nb;
+    if (t <= 0) return cudaSuccess;
+    const int blocks = (int)((t + 511) / 512 < 1024 ? (t + 511) / 512 : 1024);
+    k_concat<<<blocks, 512, 0, s>>>(dst, a, na, b, nb);
     return cudaGetLastError();
 }
 

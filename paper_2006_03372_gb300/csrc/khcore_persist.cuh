@@ -86,6 +86,7 @@ struct PersistArgs {
     const int32_t *cls_h, *cls_size, *cls_off;  // per class
     int32_t *inner;      // per class: affected vertices closer than h
     int32_t *dcount;     // per vertex: deleted vertices within h
+    int32_t *comb;       // round source list: inner vertices, then deleted ones
     int32_t ncls, hmax, alpha;
     GridSync *gs;
     PersistStats *ps;
@@ -95,10 +96,12 @@ struct PersistArgs {
 // One batch of the multi-source BFS (sources src[0..ns), h levels), every
 // block taking part; phases separated by barriers. Returns false on timeout.
 template <int W>
-__device__ bool bfs_batch(const PersistArgs &a, const int32_t *src, int32_t ns, int32_t h, int32_t *rowcnt)
+__device__ bool bfs_batch(const PersistArgs &a, const int32_t *src, int32_t ns, int32_t h, int32_t *rowcnt,
+                          int32_t row_first)
 {
     BfsBufs b = a.b;
     b.rowcnt = rowcnt;
+    b.row_first = row_first;
     LevelCtl *ctl = b.ctl;
     // reset the level ring and place the sources (level 0)
     if (!grid_sync(a.gs, a.timeout_ns, [&] {
@@ -161,12 +164,13 @@ __device__ bool bfs_batch(const PersistArgs &a, const int32_t *src, int32_t ns, 
 
 // h-degrees of src[0..ns) in batches of 64*W sources.
 template <int W>
-__device__ bool bfs_sources(const PersistArgs &a, const int32_t *src, int32_t ns, int32_t h, int32_t *rowcnt)
+__device__ bool bfs_sources(const PersistArgs &a, const int32_t *src, int32_t ns, int32_t h, int32_t *rowcnt,
+                            int32_t row_first)
 {
     constexpr int32_t S = 64 * W;
     for (int32_t off = 0; off < ns; off += S) {
         const int32_t cur = ns - off < S ? ns - off : S;
-        if (!bfs_batch<W>(a, src + off, cur, h, rowcnt)) return false;
+        if (!bfs_batch<W>(a, src + off, cur, h, rowcnt, row_first > off ? row_first - off : 0)) return false;
         if (blockIdx.x == 0 && threadIdx.x == 0) a.ps->source_batches++;
     }
     return true;
@@ -216,10 +220,18 @@ __global__ void __launch_bounds__(kBlock, (W <= 4 ? 2 : 1)) k_decompose(PersistA
             const int32_t nd = *((volatile int32_t *)&a.p.nDc[c]);
             if (na == 0) continue;
             int32_t *Ac = a.A + a.cls_off[c];
-            if (ni > 0 && !bfs_sources<W>(a, Ac, ni, a.cls_h[c], nullptr)) return;
+            const bool count_d = na > ni && !single;
+            const int32_t total = ni + (count_d ? nd : 0);
+            if (total > 0) {
+                // one source list: inner vertices, then the deleted vertices
+                // whose row counts update the outer shell (the barrier keeps
+                // the previous class's batch from still reading the list)
+                if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
+                dev_concat(a.comb, Ac, ni, a.dcls + a.cls_off[c], count_d ? nd : 0);
+                if (!bfs_sources<W>(a, a.comb, total, a.cls_h[c], count_d ? a.dcount : nullptr, ni)) return;
+            }
             if (blockIdx.x == 0 && threadIdx.x == 0) a.ps->recomputed_total += ni;
             if (na > ni) {
-                if (!single && !bfs_sources<W>(a, a.dcls + a.cls_off[c], nd, a.cls_h[c], a.dcount)) return;
                 if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
                 dev_apply_dcount(Ac, ni, na, single ? nullptr : a.dcount, a.deg);
             }
@@ -253,6 +265,7 @@ cudaError_t persist_launch_w(const PersistLaunch &L, int grid, cudaStream_t s)
     a.cls_off = L.cls_off;
     a.inner = L.inner;
     a.dcount = L.dcount;
+    a.comb = L.comb;
     a.ncls = L.ncls;
     a.hmax = L.hmax;
     a.alpha = L.alpha;

@@ -204,3 +204,27 @@ def test_barrier_wait_limit_returns_etimeout_and_recovers(kh):
         assert ei.value.status == 4
         kh.khcore_set_wait_limit(ctx.ctx, 10 ** 10)
         assert (ctx.decompose(2) == want).all()
+
+
+def test_hdegrees_of_listed_vertices(kh):
+    g = gg.chung_lu(5000, 10.0, 2.5, 400.0, 31)
+    rng = gg.Stream(4, "listed")
+    verts = np.argsort(rng.u64(g.n), kind="stable")[:777].astype(np.int32)
+    with kh.KHCore.from_graph(g) as ctx:
+        for h in (1, 2, 3):
+            got = kh.khcore_hdegrees_of(ctx.ctx, h, verts)
+            assert (got == oracle.hdegree_list(g, h, verts)).all()
+        with pytest.raises(kh.KHCoreError):
+            kh.khcore_hdegrees_of(ctx.ctx, 2, np.array([3, 3], dtype=np.int32))
+
+
+def test_round_words_and_loops_agree(kh):
+    g = gg.chung_lu(4000, 8.0, 2.5, 300.0, 41)
+    want = oracle.peel(g, 2)
+    for wr in (1, 2, 4, 8, 16):
+        for loop in (0, 1):
+            with kh.KHCore.from_graph(g, loop=loop) as ctx:
+                kh.khcore_set_round_words(ctx.ctx, wr)
+                c, r, st = ctx.decompose_ex(2)
+                assert (c == want).all(), (wr, loop)
+                assert st["recomputed_total"] <= st["affected_total"]
