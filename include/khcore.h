@@ -72,22 +72,23 @@ typedef struct {
     int64_t edges_traversed;   /* CSR entries a plain single-source h-bounded BFS
                                   would scan, summed over every source of every
                                   h-degree computation of the call */
-    /* Per-phase BFS level kernels (the initial pass, and the rounds when they
-     * are host-driven); count and time only while profiling is on
-     * (khcore_set_profiling): */
+    /* The BFS level kernels of the initial all-vertex pass: count and time
+     * only while profiling is on (khcore_set_profiling): */
     int64_t level_launches;    /* level kernel launches timed */
     double level_ms;           /* their summed device time (CUDA events) */
-    double level_bytes;        /* algorithmic bytes of those levels: per level
-                                  4*n_b + 4*m_b + 16*W*n_b for the n_b alive
-                                  rows and m_b CSR entries it scans */
+    double level_bytes;        /* algorithmic bytes of the initial pass's levels.
+                                  Per level, pull: 4*n_b + 4*m_b + 16*W*n_b for
+                                  the n_b alive rows and their m_b CSR entries;
+                                  push: (4 + 16*W) per frontier CSR entry plus
+                                  8*W per frontier vertex */
     int64_t recomputed_total;  /* affected vertices whose h-degree was recomputed
                                   by BFS (those closer than h to the deleted set);
                                   the others were updated by counting */
     double init_ms;            /* device time of the initial all-vertex h-degree pass */
     double round_ms;           /* device time of the peel rounds (with the persistent
                                   round loop: the one kernel's duration) */
-    double round_bytes;        /* algorithmic bytes of the BFS levels run in the rounds
-                                  (same per-level formula as level_bytes) */
+    double round_bytes;        /* algorithmic bytes of the BFS levels run in the
+                                  rounds (same per-level formula) */
 } khcore_stats;
 
 /*

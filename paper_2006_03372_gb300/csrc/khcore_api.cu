@@ -64,6 +64,7 @@ struct khcore_ctx {
     LevelCtl *ctl = nullptr;
     int32_t *cnt = nullptr;
     unsigned long long *edges = nullptr;  // device counter of plain-BFS-equivalent edges
+    unsigned long long *alg = nullptr;    // device counter of algorithmic bytes of the BFS levels
     int32_t push_alpha = 16;              // push when frontier degree sum * alpha < alive CSR entries
     int32_t round_loop = 0;               // 0: one persistent launch per decomposition, 1: host-driven rounds
     unsigned long long wait_limit_ns = 10ull * 1000 * 1000 * 1000;  // one grid-barrier wait
@@ -310,8 +311,10 @@ khcore_status hdeg_sources(khcore_ctx *c, int W, int32_t h, const int32_t *src, 
     b.edges = c->edges;
     b.rowcnt = rowcnt;
     b.row_first = 0;
+    b.alg_bytes = c->alg;
     BfsTuning tune;
     tune.alpha = c->push_alpha;
+    tune.n_alive = (int32_t)n_b;
     tune.m_alive = (unsigned long long)m_b;
     const int32_t S = 64 * W;
     const int grid = bfs_grid(c, W);
@@ -326,7 +329,6 @@ khcore_status hdeg_sources(khcore_ctx *c, int W, int32_t h, const int32_t *src, 
                          stt ? &stt->kernel_launches : nullptr, c->profiling ? &c->timer : nullptr));
         if (stt) {
             stt->source_batches++;
-            stt->level_bytes += (double)h * (4.0 * n_b + 4.0 * m_b + 16.0 * W * n_b);
         }
     }
     return KHCORE_OK;
@@ -406,6 +408,7 @@ khcore_status setup_ctx(khcore_ctx *c, const std::vector<int32_t> &rp, const std
     A(dev_alloc(&c->vis, nw));
     A(dev_alloc(&c->st, 1));
     A(dev_alloc(&c->edges, 1));
+    A(dev_alloc(&c->alg, 1));
     A(dev_alloc(&c->flag[0], nflag));
     A(dev_alloc(&c->flag[1], nflag));
     for (int k = 0; k < 3; k++) {
@@ -464,9 +467,10 @@ khcore_status finish_decompose(khcore_ctx *c, int32_t G, int32_t *core_out, int3
     CU(cudaEventRecord(c->ev1, c->stream));
     if ((s = write_out(c, core_out, c->core)) != KHCORE_OK) return s;
     if ((s = write_out(c, round_out, c->rnd)) != KHCORE_OK) return s;
-    unsigned long long edges = 0;
+    unsigned long long edges = 0, alg = 0;
     std::vector<int32_t> kg(G);
     CU(cudaMemcpyAsync(&edges, c->edges, sizeof edges, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(&alg, c->alg, sizeof alg, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaMemcpyAsync(kg.data(), c->kg, sizeof(int32_t) * G, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     float ms = 0.f, ms_init = 0.f;
@@ -476,6 +480,7 @@ khcore_status finish_decompose(khcore_ctx *c, int32_t G, int32_t *core_out, int3
     stt.init_ms = ms_init;
     stt.round_ms = ms - ms_init;
     stt.edges_traversed = (int64_t)edges;
+    stt.round_bytes = (double)alg - stt.level_bytes;  // every level after the initial pass
     stt.k_max = *std::max_element(kg.begin(), kg.end());
     if (persistent) {
         if ((s = flush_timer(c)) != KHCORE_OK) return s;  // the initial pass's level launches
@@ -580,6 +585,7 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
     CU(cudaMemsetAsync(c->inner, 0, sizeof(int32_t) * ncls, c->stream));
     CU(cudaMemcpyAsync(c->cls_src, cls_src.data(), sizeof(int32_t) * c->n, cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemsetAsync(c->edges, 0, sizeof(unsigned long long), c->stream));
+    CU(cudaMemsetAsync(c->alg, 0, sizeof(unsigned long long), c->stream));
     CU(launch_alive_init(c->alive, c->n, c->stream));
     stt.kernel_launches += 1;
     // the host vectors above must outlive the async copies
@@ -592,7 +598,10 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
             return s;
 
     CU(cudaEventRecord(c->ev_init, c->stream));
-    const double init_bytes = stt.level_bytes;
+    unsigned long long init_alg = 0;
+    CU(cudaMemcpyAsync(&init_alg, c->alg, sizeof init_alg, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    stt.level_bytes = (double)init_alg;  // the initial pass
     const int pgrid = c->round_loop == 0 ? c->sm_count * max_blocks_per_sm_persist(Wr) : 0;
     if (pgrid > 0) {
         // the whole decomposition in one cooperative launch
@@ -619,6 +628,7 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         L.b.cnt = c->cnt;
         L.b.edges = c->edges;
         L.b.rowcnt = nullptr;
+        L.b.alg_bytes = c->alg;
         L.vis = c->vis;
         L.A = c->src;
         L.dcls = c->dcls;
@@ -654,7 +664,6 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         stt.recomputed_total += psh.recomputed_total;
         stt.deleted_total += psh.deleted_total;
         stt.affected_total += psh.affected_total;
-        stt.round_bytes = psh.level_bytes;
         return finish_decompose(c, G, core_out, round_out, stats, stt, true);
     }
 
@@ -730,7 +739,6 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         CU(cudaMemcpyAsync(&c->st->round, &c->st_host->round, sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
     }
     stt.rounds = round;
-    stt.round_bytes = stt.level_bytes - init_bytes;
     return finish_decompose(c, G, core_out, round_out, stats, stt, false);
 }
 
@@ -786,7 +794,7 @@ void khcore_destroy(khcore_ctx *c)
                     c->nDc, c->inner, c->clsh, c->dcls, c->dcount, c->comb, c->cls_size, c->gs, c->pstats,
                     c->cls_src, c->alive, c->deg, c->core, c->rnd, c->src, c->vis, c->st, c->V, c->F[0], c->F[1],
                     c->flag[0], c->flag[1], c->Q[0], c->Q[1], c->Q[2], c->I[0], c->I[1], c->I[2], c->T, c->ctl,
-                    c->cnt, c->edges};
+                    c->cnt, c->edges, c->alg};
     for (void *p : bufs) cudaFree(p);
     for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
     if (c->st_host) cudaFreeHost(c->st_host);

@@ -400,6 +400,19 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
     const bool push = use_push(b.ctl, cslot, tune);
 
     for (int i = threadIdx.x; i < 64 * W; i += blockDim.x) cnt_s[i] = 0;
+    // Algorithmic bytes of this level. Pull: 4 n_b (row offsets) + 4 m_b
+    // (column ids) + 16 W n_b (own visited and next-frontier rows) over the
+    // n_b alive rows and their m_b entries. Push: the frontier rows it reads
+    // (8 W per frontier vertex) and, per frontier entry, the column id, the
+    // neighbour's visited row and its next-frontier row (4 + 16 W).
+    if (blockIdx.x == 0 && threadIdx.x == 0 && b.alg_bytes) {
+        const unsigned long long nb = (unsigned long long)tune.n_alive;
+        const unsigned long long bytes =
+            push ? (unsigned long long)b.ctl->fe[cslot] * (4ull + 16ull * W) +
+                       (unsigned long long)b.ctl->q[cslot] * 8ull * W
+                 : 4ull * nb + 4ull * tune.m_alive + 16ull * W * nb;
+        atomicAdd(b.alg_bytes, bytes);
+    }
     __syncthreads();
 
     const int lane = threadIdx.x & 31;

@@ -73,12 +73,14 @@ struct BfsBufs {
     unsigned long long *edges;
     int32_t *rowcnt;
     int32_t row_first;
+    unsigned long long *alg_bytes;  // algorithmic bytes of every level run (see dev_level)
 };
 
 // Direction choice of one level: push when (sum of frontier degrees) * alpha
 // < CSR entries of the alive graph, else pull.
 struct BfsTuning {
     int32_t alpha;
+    int32_t n_alive;
     unsigned long long m_alive;
 };
 

@@ -141,12 +141,9 @@ __device__ bool bfs_batch(const PersistArgs &a, const int32_t *src, int32_t ns, 
     BfsTuning tune;
     tune.alpha = a.alpha;
     for (int lvl = 0; lvl < h; lvl++) {
-        if (!grid_sync(a.gs, a.timeout_ns, [&] {
-                a.ps->level_bytes += (double)(4.0 * a.st->alive + 4.0 * (double)a.st->m_alive + 16.0 * W * a.st->alive);
-                a.ps->level_steps++;
-            }))
-            return false;
+        if (!grid_sync(a.gs, a.timeout_ns, [&] { a.ps->level_steps++; })) return false;
         tune.m_alive = *((volatile unsigned long long *)&a.st->m_alive);
+        tune.n_alive = *((volatile int32_t *)&a.st->alive);
         if (lvl == h - 1)
             dev_level<W, true>(a.g, a.alive, b, lvl, tune);
         else
