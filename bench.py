@@ -132,6 +132,17 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """The largest value over all ranks (the slowest rank's time); the value
+    itself without a process group. Works with the nccl and gloo backends."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -275,9 +286,7 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, pg, "cuda")
         pg.barrier()
     ms_per_step = ms / args.steps
     value = world * args.steps * len(hs) / (ms / 1e3)
@@ -320,9 +329,7 @@ def run_ours(args):
         e2e_times.append(time.perf_counter() - t0)
     e2e_s = statistics.median(e2e_times)
     if pg:
-        t = torch.tensor([e2e_s], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e2e_s, pg, "cuda")
 
     st_last = {h: stats[-len(hs) + i] for i, h in enumerate(hs)}
     line = {
