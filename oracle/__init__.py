@@ -57,6 +57,8 @@ def _load():
         lib.orc_hdegree_list.restype = ctypes.c_int
         lib.orc_peel.argtypes = [i32, P, P, i32, P, P]
         lib.orc_peel.restype = ctypes.c_int
+        lib.orc_peel_bounded.argtypes = [i32, P, P, i32, P, i64, P, P]
+        lib.orc_peel_bounded.restype = ctypes.c_int64
         lib.orc_bruteforce.argtypes = [i32, P, i32, P]
         lib.orc_bruteforce.restype = ctypes.c_int
         lib.orc_kcore_bz.argtypes = [i32, P, P, P]
@@ -131,6 +133,21 @@ def peel(g, h: int, return_order: bool = False):
     if return_order:
         return core[: g.n], order[: g.n]
     return core[: g.n]
+
+
+def peel_bounded(g, h: int, max_removed: int, deg_init=None):
+    """Algorithm 1 stopped after max_removed removals (optionally from given
+    initial h-degrees). Returns (removed, core, order); core/order are valid
+    for the first `removed` vertices of order."""
+    lib = _load()
+    rp, col = _csr(g)
+    core = np.full(max(g.n, 1), -1, dtype=np.int32)
+    order = np.full(max(g.n, 1), -1, dtype=np.int32)
+    d = None if deg_init is None else np.ascontiguousarray(deg_init, dtype=np.int32)
+    r = lib.orc_peel_bounded(g.n, _p(rp), _p(col), int(h), _p(d), int(max_removed), _p(core), _p(order))
+    if r < 0:
+        raise MemoryError("oracle: out of memory")
+    return int(r), core[: g.n], order[: g.n]
 
 
 def adjacency_masks(g) -> np.ndarray:

@@ -150,8 +150,23 @@ int orc_hdegree_list(int32_t n, const int32_t *row_ptr, const int32_t *col,
 /* bucket index; core_out[v] receives k at v's removal. order_out (nullable) */
 /* receives the vertices in removal order. Returns 0, or -1 on ENOMEM.       */
 /* ------------------------------------------------------------------------ */
+/* orc_peel_bounded: the same algorithm, optionally starting from given
+ * h-degrees (deg_init, nullable: computed here otherwise) and stopping after
+ * max_removed removals (< 0: run to the end). Returns the number of vertices
+ * removed, or -1 on ENOMEM. Used to time the oracle on a bounded sample. */
+int64_t orc_peel_bounded(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t h,
+                         const int32_t *deg_init, int64_t max_removed, int32_t *core_out, int32_t *order_out);
+
 int orc_peel(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t h,
              int32_t *core_out, int32_t *order_out)
+{
+    int64_t r = orc_peel_bounded(n, row_ptr, col, h, NULL, -1, core_out, order_out);
+    if (r < 0) return -1;
+    return r == n ? 0 : -2;
+}
+
+int64_t orc_peel_bounded(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t h,
+                         const int32_t *deg_init, int64_t max_removed, int32_t *core_out, int32_t *order_out)
 {
     if (n == 0) return 0;
     size_t N = (size_t)n;
@@ -173,7 +188,7 @@ int orc_peel(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t h,
 
     /* lines 2-4: h-degree of every vertex, then its bucket */
     for (int32_t v = 0; v < n; v++)
-        deg[v] = (int32_t)bfs_count(v, h, row_ptr, col, alive, dist, queue, NULL, NULL);
+        deg[v] = deg_init ? deg_init[v] : (int32_t)bfs_count(v, h, row_ptr, col, alive, dist, queue, NULL, NULL);
     for (int32_t v = n - 1; v >= 0; v--) {
         int32_t b = deg[v];
         bucket[v] = b;
@@ -183,10 +198,11 @@ int orc_peel(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t h,
         head[b] = v;
     }
 
-    int32_t removed = 0;
+    int64_t removed = 0;
     /* lines 5-12, with k starting at 0 (isolated vertices have d^h = 0) */
     for (int32_t k = 0; k < n; k++) {
         while (head[k] >= 0) {
+            if (max_removed >= 0 && removed >= max_removed) goto done;
             /* lines 7-8: pick and remove a vertex of B[k]; its core index is k */
             int32_t v = head[k];
             head[k] = next[v];
@@ -219,9 +235,10 @@ int orc_peel(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t h,
             }
         }
     }
+done:
     free(deg); free(head); free(next); free(prev); free(bucket);
     free(alive); free(dist); free(queue); free(ball);
-    return removed == n ? 0 : -2;
+    return removed;
 }
 
 /* ------------------------------------------------------------------------ */

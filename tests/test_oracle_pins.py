@@ -263,3 +263,12 @@ def test_hdegree_list_scanned_edges_closed_form():
     s = gg.star(8)
     d, sc = oracle.hdegree_list(s, 2, [0, 3], return_scanned=True)
     assert list(d) == [7, 7] and list(sc) == [7 + 7 * 1, 1 + 7]
+
+
+def test_peel_bounded_is_a_prefix_of_the_full_peel():
+    g = gg.erdos_renyi_gnm(300, 900, 21)
+    core, order = oracle.peel(g, 2, return_order=True)
+    r, c2, o2 = oracle.peel_bounded(g, 2, 57)
+    assert r == 57 and (o2[:57] == order[:57]).all() and (c2[o2[:57]] == core[order[:57]]).all()
+    r, c3, o3 = oracle.peel_bounded(g, 2, -1, deg_init=oracle.hdegrees(g, 2))
+    assert r == g.n and (c3 == core).all()
