@@ -215,6 +215,19 @@ khcore_status khcore_set_round_words(khcore_ctx *ctx, int32_t words);
 khcore_status khcore_set_push_alpha(khcore_ctx *ctx, int32_t alpha);
 
 /*
+ * khcore_set_lazy — (default on) keep, for every alive vertex, an upper bound
+ * on its h-degree (decremented exactly by the deleted vertices it can still
+ * reach) and a lower bound (the upper bound minus the most it can have lost
+ * besides: the vertices within h-1 of the deleted set, Observation 2), and
+ * recompute exactly only the vertices whose lower bound does not rule out
+ * being peeled at the coming level. Every alive vertex's h-degree is at least
+ * the current level, so the peeled sets, core indices and rounds are
+ * identical to the eager mode (0: recompute every affected vertex closer
+ * than h to the deleted set in every round).
+ */
+khcore_status khcore_set_lazy(khcore_ctx *ctx, int32_t on);
+
+/*
  * khcore_set_round_loop — how the peel rounds are driven.
  *   0 (default)  the whole decomposition runs as one cooperative persistent
  *                kernel; phases are separated by grid barriers and every

@@ -43,6 +43,10 @@ struct khcore_ctx {
     int32_t *dcls = nullptr;                     // [n] deleted vertices grouped by h-class (per round)
     int32_t *dcount = nullptr;                   // [n] deleted vertices within h (outer-shell update)
     int32_t *comb = nullptr;                     // [n] round source list: inner vertices, then deleted ones
+    int32_t *slack = nullptr;                    // [n] lazy mode: deg - slack is a lower bound
+    int32_t *cand = nullptr;                     // [n] lazy mode: exact-recompute list (class regions)
+    int32_t *mind = nullptr, *minub = nullptr, *ncand = nullptr;  // [G]
+    bool lazy = true;                            // bounds instead of recomputing every inner vertex
 
     // peel state (device)
     uint32_t *alive = nullptr;
@@ -50,7 +54,7 @@ struct khcore_ctx {
     uint32_t *vis = nullptr;
     PeelState *st = nullptr;
     PeelState *st_host = nullptr;  // pinned mirror
-    int32_t *nAc_host = nullptr;   // pinned mirror of nAc, inner, nDc (3 x G)
+    int32_t *nAc_host = nullptr;   // pinned mirror of nAc, inner, nDc, ncand (4 x G)
 
     // BFS buffers, sized for W_alloc words per vertex
     int W_req = 0;   // 0 = automatic
@@ -312,6 +316,10 @@ khcore_status hdeg_sources(khcore_ctx *c, int W, int32_t h, const int32_t *src, 
     b.rowcnt = rowcnt;
     b.row_first = 0;
     b.alg_bytes = c->alg;
+    b.slev = nullptr;
+    b.cum = nullptr;
+    b.hcnt = 0;
+    b.boff = 0;
     BfsTuning tune;
     tune.alpha = c->push_alpha;
     tune.n_alive = (int32_t)n_b;
@@ -430,13 +438,18 @@ khcore_status setup_ctx(khcore_ctx *c, const std::vector<int32_t> &rp, const std
     A(dev_alloc(&c->dcls, (size_t)n));
     A(dev_alloc(&c->dcount, (size_t)n));
     A(dev_alloc(&c->comb, (size_t)n));
+    A(dev_alloc(&c->slack, (size_t)n));
+    A(dev_alloc(&c->cand, (size_t)n));
+    A(dev_alloc(&c->mind, (size_t)c->G));
+    A(dev_alloc(&c->minub, (size_t)c->G));
+    A(dev_alloc(&c->ncand, (size_t)c->G));
     A(dev_alloc(&c->cls_size, (size_t)c->G));
     A(dev_alloc(&c->gs, 1));
     A(dev_alloc(&c->pstats, 1));
     if (c->G > 1) A(dev_alloc(&c->gid, (size_t)n));
     if (st != KHCORE_OK) return st;
     e = cudaMallocHost((void **)&c->st_host, sizeof(PeelState));
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->nAc_host, 3 * sizeof(int32_t) * (size_t)c->G);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->nAc_host, 4 * sizeof(int32_t) * (size_t)c->G);
     if (e == cudaSuccess && n) e = cudaMemsetAsync(c->dcount, 0, sizeof(int32_t) * (size_t)n, c->stream);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
@@ -562,6 +575,10 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
     pv.cls_off = c->cls_off;
     pv.nAc = c->nAc;
     pv.nDc = c->nDc;
+    pv.slack = c->lazy ? c->slack : nullptr;
+    pv.mind = c->lazy ? c->mind : nullptr;
+    pv.minub = c->lazy ? c->minub : nullptr;
+    pv.ncand = c->lazy ? c->ncand : nullptr;
 
     CU(cudaEventRecord(c->ev0, c->stream));
     PeelState init;
@@ -576,6 +593,10 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
     CU(cudaMemcpyAsync(c->st, c->st_host, sizeof(PeelState), cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemsetAsync(c->kg, 0, sizeof(int32_t) * G, c->stream));
     CU(cudaMemcpyAsync(c->ming, ming_init.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->mind, ming_init.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->minub, ming_init.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemsetAsync(c->ncand, 0, sizeof(int32_t) * G, c->stream));
+    CU(cudaMemsetAsync(c->slack, 0, sizeof(int32_t) * (size_t)c->n, c->stream));
     CU(cudaMemcpyAsync(c->hg, hg.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemcpyAsync(c->gcls, gcls.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemcpyAsync(c->cls_off, cls_off.data(), sizeof(int32_t) * ncls, cudaMemcpyHostToDevice, c->stream));
@@ -629,6 +650,10 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         L.b.edges = c->edges;
         L.b.rowcnt = nullptr;
         L.b.alg_bytes = c->alg;
+        L.b.slev = nullptr;
+        L.b.cum = nullptr;
+        L.b.hcnt = 0;
+        L.b.boff = 0;
         L.vis = c->vis;
         L.A = c->src;
         L.dcls = c->dcls;
@@ -639,6 +664,7 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         L.inner = c->inner;
         L.dcount = c->dcount;
         L.comb = c->comb;
+        L.cand = c->cand;
         L.ncls = ncls;
         L.hmax = hmax;
         L.alpha = c->push_alpha;
@@ -676,6 +702,24 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         // one round: levels, peel sets D, affected sets A, recompute deg[A];
         // the affected-BFS frontier lists reuse the BFS frontier lists Q[0..2]
         CU(launch_min_alive_deg(g, c->alive, c->deg, pv, grid, c->stream));
+        if (c->lazy) {
+            // exact recompute of the vertices whose bounds leave their fate open
+            CU(launch_refine_select(g, c->alive, c->deg, pv, c->cand, grid, c->stream));
+            CU(cudaMemcpyAsync(c->nAc_host + 3 * G, c->ncand, sizeof(int32_t) * ncls, cudaMemcpyDeviceToHost,
+                               c->stream));
+            CU(cudaStreamSynchronize(c->stream));
+            stt.kernel_launches++;
+            for (int32_t k = 0; k < ncls; k++) {
+                const int32_t nc = c->nAc_host[3 * G + k];
+                if (nc <= 0) continue;
+                if ((s = hdeg_sources(c, Wr, cls_h[k], c->cand + cls_off[k], nc, c->st_host->alive,
+                                      (int64_t)c->st_host->m_alive, &stt)) != KHCORE_OK)
+                    return s;
+                stt.recomputed_total += nc;
+                CU(launch_min_over_list(c->cand + cls_off[k], nc, c->deg, pv, c->stream));
+                stt.kernel_launches++;
+            }
+        }
         CU(launch_set_level(pv, c->st, c->stream));
         CU(launch_peel_compact(g, c->alive, c->deg, pv, c->st, c->core, c->rnd, c->vis, c->Q[0], c->dcls, grid,
                                c->stream));
@@ -717,7 +761,17 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
             const int32_t ni = std::min(c->nAc_host[G + k], na);
             const int32_t nd = c->nAc_host[2 * G + k];
             if (na == 0) continue;
-            const bool single = (ps.nD == 1);  // the outer shell loses exactly 1
+            const bool single = (ps.nD == 1);  // every affected vertex loses exactly that one
+            if (c->lazy) {
+                // row counts of the deleted set; bounds for the inner vertices
+                if (!single && (s = hdeg_sources(c, Wr, cls_h[k], c->dcls + cls_off[k], nd, ps.alive,
+                                                 (int64_t)ps.m_alive, &stt, c->dcount, 0)) != KHCORE_OK)
+                    return s;
+                CU(launch_apply_lazy(c->src + cls_off[k], ni, na, single ? nullptr : c->dcount, c->deg, c->slack,
+                                     ni + nd, c->stream));
+                stt.kernel_launches++;
+                continue;
+            }
             const bool count_d = na > ni && !single;
             // one source list: the inner vertices (their h-degrees) and, after
             // them, the deleted vertices (row counts on the outer shell)
@@ -791,7 +845,7 @@ void khcore_destroy(khcore_ctx *c)
     cudaSetDevice(c->device);
     if (c->stream && !c->failed) cudaStreamSynchronize(c->stream);
     void *bufs[] = {c->row_ptr, c->col, c->classes, c->gid, c->kg, c->ming, c->hg, c->gcls, c->cls_off, c->nAc,
-                    c->nDc, c->inner, c->clsh, c->dcls, c->dcount, c->comb, c->cls_size, c->gs, c->pstats,
+                    c->nDc, c->inner, c->clsh, c->dcls, c->dcount, c->comb, c->slack, c->cand, c->mind, c->minub, c->ncand, c->cls_size, c->gs, c->pstats,
                     c->cls_src, c->alive, c->deg, c->core, c->rnd, c->src, c->vis, c->st, c->V, c->F[0], c->F[1],
                     c->flag[0], c->flag[1], c->Q[0], c->Q[1], c->Q[2], c->I[0], c->I[1], c->I[2], c->T, c->ctl,
                     c->cnt, c->edges, c->alg};
@@ -905,6 +959,13 @@ khcore_status khcore_set_push_alpha(khcore_ctx *c, int32_t alpha)
     if (!c) return KHCORE_EINVAL;
     if (alpha < 0) return fail(c, KHCORE_EINVAL, "alpha must be >= 0 (got %d)", alpha);
     c->push_alpha = alpha;
+    return KHCORE_OK;
+}
+
+khcore_status khcore_set_lazy(khcore_ctx *c, int32_t on)
+{
+    if (!c) return KHCORE_EINVAL;
+    c->lazy = on != 0;
     return KHCORE_OK;
 }
 

@@ -148,6 +148,17 @@ __device__ __forceinline__ uint64_t row_mask(int j, int32_t row_first)
     return ~0ull << (row_first - lo);
 }
 
+// Bits of word j that a vertex y may count for (see BfsBufs::slev): source
+// positions below cum[hcnt - slev[y]]; every bit when no eligibility is set.
+__device__ __forceinline__ uint64_t elig_mask(const BfsBufs &b, int j, int32_t y)
+{
+    if (!b.slev || y < 0) return ~0ull;
+    const int32_t lim = b.cum[b.hcnt - b.slev[y]] - b.boff - 64 * j;
+    if (lim <= 0) return 0ull;
+    if (lim >= 64) return ~0ull;
+    return (1ull << lim) - 1ull;
+}
+
 // Per-thread accumulators flushed once at the end of a level kernel.
 struct Acc {
     unsigned long long scanned;  // plain-BFS-equivalent CSR entries
@@ -366,7 +377,7 @@ __device__ __forceinline__ void pull_groups(const int32_t *list, int32_t count, 
             v = V[(size_t)y * W + gi];
             nw = select_word<W>(a, gi) & ~v;
         }
-        swar_step<W>(sw, nw, cnt_s);
+        swar_step<W>(sw, nw & elig_mask(b, gi, act ? y : -1), cnt_s);
         if (b.rowcnt) {  // uniform
             int32_t rc = __popcll(nw & row_mask(gi, b.row_first));
 #pragma unroll
@@ -454,7 +465,7 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
                     }
                 }
             }
-            swar_step<W>(sw, fresh, cnt_s);
+            swar_step<W>(sw, fresh & elig_mask(b, j, y), cnt_s);
             const unsigned any = __ballot_sync(kFull, nbits != 0);
             const bool lead = (j == 0) && (((any >> (grp * W)) & gmask) != 0);
             bool claimed = false;
@@ -511,7 +522,7 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
                         v = V[(size_t)y * W + j];
                         nw = m & ~v;
                     }
-                    swar_step<W>(sw, nw, cnt_s);
+                    swar_step<W>(sw, nw & elig_mask(b, lane, act ? y : -1), cnt_s);
                     if (b.rowcnt) {
                         int32_t rc = __popcll(nw & row_mask(lane, b.row_first));
 #pragma unroll
@@ -658,8 +669,26 @@ __device__ __forceinline__ void dev_alive_init(uint32_t *alive, int32_t n)
     }
 }
 
-// Per-graph minimum of deg over alive vertices, into p.ming (atomicMin). A
-// warp whose 32 vertices belong to one graph reduces first.
+// Whole warp calls: atomicMin of m into arr[g] per graph, one atomic per warp
+// when the warp's contributing lanes share a graph (lanes with g < 0 skip).
+__device__ __forceinline__ void warp_min_by_graph(int32_t m, int32_t g, int32_t *arr)
+{
+    const unsigned act = __ballot_sync(kFull, g >= 0);
+    if (!act) return;
+    const int lane = threadIdx.x & 31;
+    const int32_t g0 = __shfl_sync(kFull, g, __ffs(act) - 1);
+    if (__all_sync(kFull, g < 0 || g == g0)) {
+        int32_t r = g >= 0 ? m : INT_MAX;
+#pragma unroll
+        for (int off = 16; off; off >>= 1) r = min(r, __shfl_xor_sync(kFull, r, off));
+        if (lane == 0) atomicMin(&arr[g0], r);
+    } else if (g >= 0) {
+        atomicMin(&arr[g], m);
+    }
+}
+
+// Per-graph minimum over alive vertices: exact h-degrees into p.ming; in the
+// lazy mode, vertices with slack give their lower bound deg - slack to p.mind.
 __device__ __forceinline__ void dev_min_alive_deg(int32_t n, const uint32_t *alive,
                                                           const int32_t *deg, PeelView p)
 {
@@ -672,17 +701,74 @@ __device__ __forceinline__ void dev_min_alive_deg(int32_t n, const uint32_t *ali
         const uint32_t aw = alive[w];
         if (!aw) continue;  // warp-uniform
         const bool a = v < n && ((aw >> lane) & 1u);
-        int32_t m = a ? deg[v] : INT_MAX;
         const int32_t gv = a ? graph_of(p, v) : -1;
-        const int32_t g0 = __shfl_sync(kFull, gv, __ffs(aw) - 1);
-        const bool uniform = __all_sync(kFull, !a || gv == g0);
-        if (uniform) {
-#pragma unroll
-            for (int off = 16; off; off >>= 1) m = min(m, __shfl_xor_sync(kFull, m, off));
-            if (lane == 0) atomicMin(&p.ming[g0], m);
-        } else if (a) {
-            atomicMin(&p.ming[gv], m);
+        const int32_t sl = (a && p.slack) ? p.slack[v] : 0;
+        const int32_t d = a ? deg[v] : INT_MAX;
+        warp_min_by_graph(d, (a && sl == 0) ? gv : -1, p.ming);
+        if (p.slack) {
+            warp_min_by_graph(d - sl, (a && sl > 0) ? gv : -1, p.mind);
+            warp_min_by_graph(d, (a && sl > 0) ? gv : -1, p.minub);
         }
+    }
+}
+
+// Lazy mode: the coming level is max(k_g, true min of graph g) <= T_g =
+// max(k_g, min(exact min, smallest upper bound with slack)). An alive vertex
+// whose lower bound deg - slack is at most T_g might be peeled at that level
+// or be the minimum; it is listed (class region of cand, p.ncand) for an
+// exact recompute and its slack dropped. Every other vertex with slack has a
+// true h-degree above T_g, so it is neither peeled nor the minimum.
+__device__ __forceinline__ void dev_refine_select(int32_t n, const uint32_t *alive, const int32_t *deg, PeelView p,
+                                                  int32_t *cand)
+{
+    const int lane = threadIdx.x & 31;
+    const int32_t nw = (n + 31) >> 5;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = warp; w < nw; w += nwarps) {
+        const uint32_t aw = alive[w];
+        if (!aw) continue;  // warp-uniform
+        const int32_t v = (int32_t)w * 32 + lane;
+        bool pick = false;
+        int32_t cv = -1;
+        if (v < n && ((aw >> lane) & 1u)) {
+            const int32_t sl = p.slack[v];
+            if (sl > 0) {
+                const int32_t g = graph_of(p, v);
+                const int32_t T = max(p.kg[g], min(p.ming[g], p.minub[g]));
+                if (p.mind[g] <= T) {
+                    if (deg[v] - sl <= T) {
+                        pick = true;
+                        cv = __ldg(&p.cls[g]);
+                        p.slack[v] = 0;
+                    }
+                }
+            }
+        }
+        const unsigned m = __ballot_sync(kFull, pick);
+        if (!m) continue;
+        const int32_t c0 = __shfl_sync(kFull, cv, __ffs(m) - 1);
+        if (__all_sync(kFull, !pick || cv == c0)) {
+            warp_append(pick, v, cand + __ldg(&p.cls_off[c0]), &p.ncand[c0]);
+        } else if (pick) {
+            cand[__ldg(&p.cls_off[cv]) + atomicAdd(&p.ncand[cv], 1)] = v;
+        }
+    }
+}
+
+// After the exact recompute of the listed vertices: fold their h-degrees into
+// the per-graph exact minimum.
+__device__ __forceinline__ void dev_min_over_list(const int32_t *list, int32_t count, const int32_t *deg, PeelView p)
+{
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < count; i0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + threadIdx.x;  // block-uniform loop
+        int32_t v = -1, d = INT_MAX, g = -1;
+        if (i < count) {
+            v = list[i];
+            d = deg[v];
+            g = graph_of(p, v);
+        }
+        warp_min_by_graph(d, g, p.ming);
     }
 }
 
@@ -694,6 +780,8 @@ __device__ __forceinline__ void dev_set_level(PeelView p, PeelState *st)
         const int32_t m = p.ming[g];
         if (m != INT_MAX && m > p.kg[g]) p.kg[g] = m;
         p.ming[g] = INT_MAX;
+        if (p.mind) p.mind[g] = INT_MAX;
+        if (p.minub) p.minub[g] = INT_MAX;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->nD = 0;
@@ -703,6 +791,7 @@ __device__ __forceinline__ void dev_set_level(PeelView p, PeelState *st)
     for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < p.ncls; c += gridDim.x * blockDim.x) {
         p.nAc[c] = 0;
         p.nDc[c] = 0;
+        if (p.ncand) p.ncand[c] = 0;
     }
 }
 
@@ -834,6 +923,26 @@ __device__ __forceinline__ void dev_apply_dcount(const int32_t *list, int32_t in
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t u = list[i];
         if (i >= inner) deg[u] -= dcount ? dcount[u] : 1;
+        if (dcount) dcount[u] = 0;
+    }
+}
+
+// Lazy mode update of the affected list[0..total): every vertex loses the
+// deleted vertices within h hops (dcount, or 1 when dcount is null) for sure;
+// those closer than h (index < inner) may lose up to `extra` more vertices
+// (Observation 2: the rest of what they lose lies within h-1 of the deleted
+// set), which widens their slack. Resets dcount.
+__device__ __forceinline__ void dev_apply_lazy(const int32_t *list, int32_t inner, int32_t total, int32_t *dcount,
+                                               int32_t *deg, int32_t *slack, int32_t extra)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = list[i];
+        const int32_t d = deg[u] - (dcount ? dcount[u] : 1);
+        deg[u] = d;
+        if (i < inner) {
+            const long long sl = (long long)slack[u] + extra;
+            slack[u] = (int32_t)(sl < d ? sl : d);
+        }
         if (dcount) dcount[u] = 0;
     }
 }

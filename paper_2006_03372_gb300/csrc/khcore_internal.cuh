@@ -74,6 +74,14 @@ struct BfsBufs {
     int32_t *rowcnt;
     int32_t row_first;
     unsigned long long *alg_bytes;  // algorithmic bytes of every level run (see dev_level)
+    // Optional eligibility of the column counts (the ball-restricted label BFS
+    // of the paper's update, Algorithm 3): when slev is set, vertex y counts
+    // for source position p (in the whole source list) only if
+    // p < cum[hcnt - slev[y]]; boff is the batch's first position.
+    const int32_t *slev;
+    const int32_t *cum;
+    int32_t hcnt;
+    int32_t boff;
 };
 
 // Direction choice of one level: push when (sum of frontier degrees) * alpha
@@ -117,6 +125,12 @@ struct PeelView {
     const int32_t *cls_off;  // [ncls] start of each class's region of the source list
     int32_t *nAc;            // [ncls] affected vertices per class this round
     int32_t *nDc;            // [ncls] deleted vertices per class this round
+    // Lazy mode (slack != nullptr): deg[v] is an upper bound on v's h-degree
+    // and deg[v] - slack[v] a lower bound (slack 0 = exact).
+    int32_t *slack;          // [n]
+    int32_t *mind;           // [G] min over alive vertices with slack of deg - slack
+    int32_t *minub;          // [G] min over alive vertices with slack of deg
+    int32_t *ncand;          // [ncls] vertices picked for an exact recompute this round
 };
 
 // ---- launchers (khcore_kernels.cu) -----------------------------------------
@@ -157,6 +171,13 @@ cudaError_t launch_apply_dcount(const int32_t *list, int32_t inner, int32_t tota
 cudaError_t launch_affected_level(const GraphView &g, const uint32_t *alive, int lvl, int32_t *const aq[3],
                                   uint32_t *vis, const PeelView &p, PeelState *st, int32_t *A, int last, int grid,
                                   cudaStream_t s);
+// Lazy mode (see dev_refine_select, dev_min_over_list, dev_apply_lazy).
+cudaError_t launch_refine_select(const GraphView &g, const uint32_t *alive, const int32_t *deg, const PeelView &p,
+                                 int32_t *cand, int grid, cudaStream_t s);
+cudaError_t launch_min_over_list(const int32_t *list, int32_t count, const int32_t *deg, const PeelView &p,
+                                 cudaStream_t s);
+cudaError_t launch_apply_lazy(const int32_t *list, int32_t inner, int32_t total, int32_t *dcount, int32_t *deg,
+                              int32_t *slack, int32_t extra, cudaStream_t s);
 // dst = a[0..na) followed by b[0..nb).
 cudaError_t launch_concat(int32_t *dst, const int32_t *a, int32_t na, const int32_t *b, int32_t nb, cudaStream_t s);
 // st->nA = sum of p.nAc.
@@ -205,6 +226,7 @@ struct PersistLaunch {
     int32_t *inner;
     int32_t *dcount;
     int32_t *comb;  // [n] round source list
+    int32_t *cand;  // [n] lazy mode: vertices to recompute exactly (class regions)
     int32_t ncls, hmax, alpha;
     GridSync *gs;
     PersistStats *ps;

@@ -36,6 +36,21 @@ __global__ void k_snapshot_inner(PeelView p, const int32_t *cls_h, int lvl, int3
     dev_snapshot_inner(p, cls_h, lvl, inner);
 }
 __global__ void k_sum_classes(PeelView p, PeelState *st) { dev_sum_classes(p, st); }
+__global__ void __launch_bounds__(kBlock) k_refine_select(int32_t n, const uint32_t *alive, const int32_t *deg,
+                                                          PeelView p, int32_t *cand)
+{
+    dev_refine_select(n, alive, deg, p, cand);
+}
+__global__ void __launch_bounds__(kBlock) k_min_over_list(const int32_t *list, int32_t count, const int32_t *deg,
+                                                          PeelView p)
+{
+    dev_min_over_list(list, count, deg, p);
+}
+__global__ void k_apply_lazy(const int32_t *list, int32_t inner, int32_t total, int32_t *dcount, int32_t *deg,
+                             int32_t *slack, int32_t extra)
+{
+    dev_apply_lazy(list, inner, total, dcount, deg, slack, extra);
+}
 __global__ void k_concat(int32_t *dst, const int32_t *a, int32_t na, const int32_t *b, int32_t nb)
 {
     dev_concat(dst, a, na, b, nb);
@@ -111,6 +126,31 @@ cudaError_t launch_concat(int32_t *dst, const int32_t *a, int32_t na, const int3
     if (t <= 0) return cudaSuccess;
     const int blocks = (int)((t + 511) / 512 < 1024 ? (t + 511) / 512 : 1024);
     k_concat<<<blocks, 512, 0, s>>>(dst, a, na, b, nb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine_select(const GraphView &g, const uint32_t *alive, const int32_t *deg, const PeelView &p,
+                                 int32_t *cand, int grid, cudaStream_t s)
+{
+    k_refine_select<<<grid, kBlock, 0, s>>>(g.n, alive, deg, p, cand);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_min_over_list(const int32_t *list, int32_t count, const int32_t *deg, const PeelView &p,
+                                 cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    const int blocks = (count + kBlock - 1) / kBlock < 1024 ? (count + kBlock - 1) / kBlock : 1024;
+    k_min_over_list<<<blocks, kBlock, 0, s>>>(list, count, deg, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_lazy(const int32_t *list, int32_t inner, int32_t total, int32_t *dcount, int32_t *deg,
+                              int32_t *slack, int32_t extra, cudaStream_t s)
+{
+    if (total <= 0) return cudaSuccess;
+    const int blocks = (total + 511) / 512 < 2048 ? (total + 511) / 512 : 2048;
+    k_apply_lazy<<<blocks, 512, 0, s>>>(list, inner, total, dcount, deg, slack, extra);
     return cudaGetLastError();
 }
 

@@ -87,6 +87,7 @@ struct PersistArgs {
     int32_t *inner;      // per class: affected vertices closer than h
     int32_t *dcount;     // per vertex: deleted vertices within h
     int32_t *comb;       // round source list: inner vertices, then deleted ones
+    int32_t *cand;       // lazy mode: exact-recompute list (class regions)
     int32_t ncls, hmax, alpha;
     GridSync *gs;
     PersistStats *ps;
@@ -182,6 +183,22 @@ __global__ void __launch_bounds__(kBlock, (W <= 4 ? 2 : 1)) k_decompose(PersistA
         // level of every graph: k_g <- max(k_g, min alive h-degree)
         if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
         dev_min_alive_deg(a.g.n, a.alive, a.deg, a.p);
+        if (a.p.slack) {
+            // lazy mode: exact recompute of the vertices whose bounds leave
+            // their fate at the coming level open
+            if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
+            dev_refine_select(a.g.n, a.alive, a.deg, a.p, a.cand);
+            for (int32_t c = 0; c < a.ncls; c++) {
+                if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
+                const int32_t nc = *((volatile int32_t *)&a.p.ncand[c]);
+                if (nc <= 0) continue;
+                const int32_t *cl = a.cand + a.cls_off[c];
+                if (!bfs_sources<W>(a, cl, nc, a.cls_h[c], nullptr, 0)) return;
+                if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
+                dev_min_over_list(cl, nc, a.deg, a.p);
+                if (blockIdx.x == 0 && threadIdx.x == 0) a.ps->recomputed_total += nc;
+            }
+        }
         if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
         dev_set_level(a.p, a.st);
         // peel set D
@@ -217,6 +234,14 @@ __global__ void __launch_bounds__(kBlock, (W <= 4 ? 2 : 1)) k_decompose(PersistA
             const int32_t nd = *((volatile int32_t *)&a.p.nDc[c]);
             if (na == 0) continue;
             int32_t *Ac = a.A + a.cls_off[c];
+            if (a.p.slack) {
+                // lazy mode: row counts of the deleted set, bounds for the rest
+                if (!single && nd > 0 && !bfs_sources<W>(a, a.dcls + a.cls_off[c], nd, a.cls_h[c], a.dcount, 0))
+                    return;
+                if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
+                dev_apply_lazy(Ac, ni, na, single ? nullptr : a.dcount, a.deg, a.p.slack, ni + nd);
+                continue;
+            }
             const bool count_d = na > ni && !single;
             const int32_t total = ni + (count_d ? nd : 0);
             if (total > 0) {
@@ -263,6 +288,7 @@ cudaError_t persist_launch_w(const PersistLaunch &L, int grid, cudaStream_t s)
     a.inner = L.inner;
     a.dcount = L.dcount;
     a.comb = L.comb;
+    a.cand = L.cand;
     a.ncls = L.ncls;
     a.hmax = L.hmax;
     a.alpha = L.alpha;

@@ -228,3 +228,22 @@ def test_round_words_and_loops_agree(kh):
                 c, r, st = ctx.decompose_ex(2)
                 assert (c == want).all(), (wr, loop)
                 assert st["recomputed_total"] <= st["affected_total"]
+
+
+@pytest.mark.parametrize("loop", [0, 1])
+def test_lazy_bounds_and_eager_recompute_agree(kh, loop):
+    """The bound-based mode (default) and the eager mode peel the same sets at
+    the same levels: core indices and rounds equal, and equal the oracle."""
+    graphs = [gg.chung_lu(600, 6.0, 2.5, 60.0, 43), gg.chung_lu(500, 5.0, 2.1, 80.0, 44)] \
+        + list(small_graphs(60, 4, (2, 200)))
+    for g in graphs:
+        for h in (2, 3, 4):
+            want = oracle.peel(g, h)
+            out = {}
+            for lazy in (0, 1):
+                with kh.KHCore.from_graph(g, loop=loop, lazy=lazy) as ctx:
+                    out[lazy] = ctx.decompose_ex(h)
+            (c0, r0, s0), (c1, r1, s1) = out[0], out[1]
+            assert (c0 == want).all() and (c1 == want).all(), (g.name, h)
+            assert (r0 == r1).all() and s0["rounds"] == s1["rounds"], (g.name, h)
+            assert s1["recomputed_total"] <= s0["recomputed_total"] + g.n, (g.name, h)
