@@ -220,10 +220,11 @@ khcore_status khcore_set_push_alpha(khcore_ctx *ctx, int32_t alpha);
  * reach) and a lower bound (the upper bound minus the most it can have lost
  * besides: the vertices within h-1 of the deleted set, Observation 2), and
  * recompute exactly only the vertices whose lower bound does not rule out
- * being peeled at the coming level. Every alive vertex's h-degree is at least
- * the current level, so the peeled sets, core indices and rounds are
- * identical to the eager mode (0: recompute every affected vertex closer
- * than h to the deleted set in every round).
+ * being peeled at the coming level. That level is at most T = max(k, least
+ * exact h-degree, least upper bound), so a vertex whose lower bound exceeds T
+ * is neither peeled at it nor sets it: the peeled sets, core indices and
+ * rounds are identical to the eager mode (0: recompute every affected vertex
+ * closer than h to the deleted set in every round).
  */
 khcore_status khcore_set_lazy(khcore_ctx *ctx, int32_t on);
 
