@@ -45,6 +45,7 @@ struct khcore_ctx {
     int32_t *comb = nullptr;                     // [n] round source list: inner vertices, then deleted ones
     int32_t *slack = nullptr;                    // [n] lazy mode: deg - slack is a lower bound
     int32_t *cand = nullptr;                     // [n] lazy mode: exact-recompute list (class regions)
+    int32_t *wsum = nullptr;                     // [n] lazy mode: ball bounds of the deleted set, zero between rounds
     int32_t *mind = nullptr, *minub = nullptr, *ncand = nullptr;  // [G]
     bool lazy = true;                            // bounds instead of recomputing every inner vertex
 
@@ -272,6 +273,7 @@ khcore_status clear_if_dirty(khcore_ctx *c)
     CU(cudaMemsetAsync(c->flag[1], 0, nflag, c->stream));
     CU(cudaMemsetAsync(c->cnt, 0, (size_t)64 * c->W_alloc * sizeof(int32_t), c->stream));
     CU(cudaMemsetAsync(c->dcount, 0, sizeof(int32_t) * (size_t)std::max(c->n, 1), c->stream));
+    CU(cudaMemsetAsync(c->wsum, 0, sizeof(int32_t) * (size_t)std::max(c->n, 1), c->stream));
     c->dirty = false;
     return KHCORE_OK;
 }
@@ -295,8 +297,11 @@ khcore_status flush_timer(khcore_ctx *c)
 // n_b / m_b: alive rows and their CSR entries (direction choice and
 // algorithmic bytes).
 // rowcnt (nullable): row counts of the sources at list positions >= row_first.
+// wsum (nullable, lazy mode with src = the deleted set): ball bounds of the
+// sources for the vertices they reach within h-1 (dev_weight_pass).
 khcore_status hdeg_sources(khcore_ctx *c, int W, int32_t h, const int32_t *src, int32_t ns, int64_t n_b,
-                           int64_t m_b, khcore_stats *stt, int32_t *rowcnt = nullptr, int32_t row_first = 0)
+                           int64_t m_b, khcore_stats *stt, int32_t *rowcnt = nullptr, int32_t row_first = 0,
+                           int32_t *wsum = nullptr)
 {
     const GraphView g = c->view();
     BfsBufs b;
@@ -320,6 +325,8 @@ khcore_status hdeg_sources(khcore_ctx *c, int W, int32_t h, const int32_t *src, 
     b.cum = nullptr;
     b.hcnt = 0;
     b.boff = 0;
+    b.wsum = wsum;
+    b.wdeg = c->deg;
     BfsTuning tune;
     tune.alpha = c->push_alpha;
     tune.n_alive = (int32_t)n_b;
@@ -440,6 +447,7 @@ khcore_status setup_ctx(khcore_ctx *c, const std::vector<int32_t> &rp, const std
     A(dev_alloc(&c->comb, (size_t)n));
     A(dev_alloc(&c->slack, (size_t)n));
     A(dev_alloc(&c->cand, (size_t)n));
+    A(dev_alloc(&c->wsum, (size_t)n));
     A(dev_alloc(&c->mind, (size_t)c->G));
     A(dev_alloc(&c->minub, (size_t)c->G));
     A(dev_alloc(&c->ncand, (size_t)c->G));
@@ -597,6 +605,7 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
     CU(cudaMemcpyAsync(c->minub, ming_init.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemsetAsync(c->ncand, 0, sizeof(int32_t) * G, c->stream));
     CU(cudaMemsetAsync(c->slack, 0, sizeof(int32_t) * (size_t)c->n, c->stream));
+    CU(cudaMemsetAsync(c->wsum, 0, sizeof(int32_t) * (size_t)c->n, c->stream));
     CU(cudaMemcpyAsync(c->hg, hg.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemcpyAsync(c->gcls, gcls.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemcpyAsync(c->cls_off, cls_off.data(), sizeof(int32_t) * ncls, cudaMemcpyHostToDevice, c->stream));
@@ -654,6 +663,9 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         L.b.cum = nullptr;
         L.b.hcnt = 0;
         L.b.boff = 0;
+        L.b.wsum = nullptr;
+        L.b.wdeg = c->deg;
+        L.wsum = c->lazy ? c->wsum : nullptr;
         L.vis = c->vis;
         L.A = c->src;
         L.dcls = c->dcls;
@@ -765,10 +777,10 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
             if (c->lazy) {
                 // row counts of the deleted set; bounds for the inner vertices
                 if (!single && (s = hdeg_sources(c, Wr, cls_h[k], c->dcls + cls_off[k], nd, ps.alive,
-                                                 (int64_t)ps.m_alive, &stt, c->dcount, 0)) != KHCORE_OK)
+                                                 (int64_t)ps.m_alive, &stt, c->dcount, 0, c->wsum)) != KHCORE_OK)
                     return s;
                 CU(launch_apply_lazy(c->src + cls_off[k], ni, na, single ? nullptr : c->dcount, c->deg, c->slack,
-                                     ni + nd, c->stream));
+                                     ni + nd, c->wsum, c->dcls + cls_off[k], c->row_ptr, cls_h[k], c->stream));
                 stt.kernel_launches++;
                 continue;
             }
@@ -817,6 +829,7 @@ khcore_status create_common(int32_t G, const std::vector<int64_t> &v_off, std::v
 
 }  // namespace
 
+
 extern "C" {
 
 const char *khcore_status_string(khcore_status s)
@@ -845,7 +858,7 @@ void khcore_destroy(khcore_ctx *c)
     cudaSetDevice(c->device);
     if (c->stream && !c->failed) cudaStreamSynchronize(c->stream);
     void *bufs[] = {c->row_ptr, c->col, c->classes, c->gid, c->kg, c->ming, c->hg, c->gcls, c->cls_off, c->nAc,
-                    c->nDc, c->inner, c->clsh, c->dcls, c->dcount, c->comb, c->slack, c->cand, c->mind, c->minub, c->ncand, c->cls_size, c->gs, c->pstats,
+                    c->nDc, c->inner, c->clsh, c->dcls, c->dcount, c->comb, c->slack, c->wsum, c->cand, c->mind, c->minub, c->ncand, c->cls_size, c->gs, c->pstats,
                     c->cls_src, c->alive, c->deg, c->core, c->rnd, c->src, c->vis, c->st, c->V, c->F[0], c->F[1],
                     c->flag[0], c->flag[1], c->Q[0], c->Q[1], c->Q[2], c->I[0], c->I[1], c->I[2], c->T, c->ctl,
                     c->cnt, c->edges, c->alg};

@@ -33,6 +33,13 @@ __global__ void __launch_bounds__(kBlock) k_end(BfsBufs b, const int32_t *src, i
 }
 
 template <int W>
+__global__ void __launch_bounds__(kBlock) k_weight_pass(BfsBufs b, const int32_t *src, const int32_t *rp,
+                                                        const uint32_t *alive, int last_radius)
+{
+    dev_weight_pass<W>(b, src, rp, alive, last_radius != 0);
+}
+
+template <int W>
 cudaError_t bfs_batch_t(const GraphView &g, const uint32_t *alive, const BfsBufs &b, const int32_t *src,
                         int32_t ns, int32_t h, int32_t *deg, BfsTuning tune, int grid, cudaStream_t s,
                         int64_t *launches, LevelTimer *timer)
@@ -56,6 +63,10 @@ cudaError_t bfs_batch_t(const GraphView &g, const uint32_t *alive, const BfsBufs
         else
             k_post<W, false><<<grid, kBlock, 0, s>>>(g, b, lvl, tune);
         l += 2;
+        if (b.wsum && (lvl == h - 2 || lvl == h - 3)) {
+            k_weight_pass<W><<<grid, kBlock, 0, s>>>(b, src, g.row_ptr, alive, lvl == h - 2);
+            l++;
+        }
     }
     k_end<W><<<grid, kBlock, 0, s>>>(b, src, ns, deg);
     l++;

@@ -622,6 +622,42 @@ __device__ __forceinline__ void dev_post(GraphView g, BfsBufs b, int lvl, BfsTun
     if (lane == 0 && scanned) atomicAdd(b.edges, scanned);
 }
 
+// Lazy-mode bound on what an alive u loses besides the deleted vertices it
+// reaches through survivors. Every such lost vertex lies, on some shortest
+// path from u, beyond the first deleted vertex d on it: within h - s hops of
+// d, where s = dist(u, d) through survivors, 1 <= s <= h-1 (Observation 2).
+// So the loss is at most the sum over deleted d within h-1 of u of the size
+// of d's (h-s)-ball: at most d's h-degree bound wdeg[d], and at most its row
+// length when h - s = 1. Called after the level that completes the sources
+// within `radius` hops: radius h-1 adds min(row length, wdeg) per source bit,
+// radius h-2 adds the rest, wdeg - min(row length, wdeg), for the sources
+// already that close. One thread per vertex of T; plain adds (each vertex is
+// once in T), saturating at INT_MAX.
+template <int W>
+__device__ __forceinline__ void dev_weight_pass(const BfsBufs &b, const int32_t *src, const int32_t *rp,
+                                                const uint32_t *alive, bool last_radius)
+{
+    const int32_t nt = b.ctl->t;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nt; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = b.T[i];
+        if (!is_alive(alive, u)) continue;
+        long long sum = 0;
+#pragma unroll 1
+        for (int j = 0; j < W; j++) {
+            uint64_t w = b.V[(size_t)u * W + j];
+            while (w) {
+                const int p = __ffsll((long long)w) - 1;
+                w &= w - 1;
+                const int32_t d = src[j * 64 + p];
+                const int32_t wd = b.wdeg[d];
+                const int32_t r1 = min(rp[d + 1] - rp[d], wd);
+                sum += last_radius ? r1 : wd - r1;
+            }
+        }
+        if (sum) b.wsum[u] = (int32_t)min((long long)b.wsum[u] + sum, (long long)INT_MAX);
+    }
+}
+
 // End of batch: zero the V rows in T, write the h-degrees of the sources.
 template <int W>
 __device__ __forceinline__ void dev_end(BfsBufs b, const int32_t *src, int32_t ns,
@@ -928,22 +964,34 @@ __device__ __forceinline__ void dev_apply_dcount(const int32_t *list, int32_t in
 }
 
 // Lazy mode update of the affected list[0..total): every vertex loses the
-// deleted vertices within h hops (dcount, or 1 when dcount is null) for sure;
-// those closer than h (index < inner) may lose up to `extra` more vertices
-// (Observation 2: the rest of what they lose lies within h-1 of the deleted
-// set), which widens their slack. Resets dcount.
+// deleted vertices it reaches within h hops through survivors (dcount, or 1
+// when dcount is null: a single deleted vertex d1[0]) for sure; those closer
+// than h (index < inner) may lose more, which widens their slack. What more
+// they lose lies within h-1 of the deleted set (Observation 2): at most
+// `extra` (the inner count plus the deleted count), and at most the ball
+// bound of dev_weight_pass (wsum; for a single deleted vertex, its h-degree
+// bound, or its row length when h = 2). Resets dcount and wsum.
 __device__ __forceinline__ void dev_apply_lazy(const int32_t *list, int32_t inner, int32_t total, int32_t *dcount,
-                                               int32_t *deg, int32_t *slack, int32_t extra)
+                                               int32_t *deg, int32_t *slack, int32_t extra, int32_t *wsum,
+                                               const int32_t *d1, const int32_t *rp, int32_t h)
 {
+    if (!dcount && d1) {
+        const int32_t d = d1[0];
+        const int32_t wd = h == 2 ? min(deg[d], rp[d + 1] - rp[d]) : deg[d];
+        extra = min(extra, wd);
+    }
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t u = list[i];
         const int32_t d = deg[u] - (dcount ? dcount[u] : 1);
         deg[u] = d;
         if (i < inner) {
-            const long long sl = (long long)slack[u] + extra;
+            int32_t ex = extra;
+            if (dcount && wsum) ex = min(ex, wsum[u]);
+            const long long sl = (long long)slack[u] + ex;
             slack[u] = (int32_t)(sl < d ? sl : d);
         }
         if (dcount) dcount[u] = 0;
+        if (wsum) wsum[u] = 0;
     }
 }
 

@@ -82,6 +82,12 @@ struct BfsBufs {
     const int32_t *cum;
     int32_t hcnt;
     int32_t boff;
+    // Optional (lazy mode, BFS seeded at the deleted set): when wsum is set,
+    // every alive vertex the batch reaches within h-1 hops gets, in wsum, the
+    // sizes bound of the sources' balls it may lose through them (see
+    // dev_weight_pass); wdeg holds the sources' h-degree bounds.
+    int32_t *wsum;
+    const int32_t *wdeg;
 };
 
 // Direction choice of one level: push when (sum of frontier degrees) * alpha
@@ -177,7 +183,8 @@ cudaError_t launch_refine_select(const GraphView &g, const uint32_t *alive, cons
 cudaError_t launch_min_over_list(const int32_t *list, int32_t count, const int32_t *deg, const PeelView &p,
                                  cudaStream_t s);
 cudaError_t launch_apply_lazy(const int32_t *list, int32_t inner, int32_t total, int32_t *dcount, int32_t *deg,
-                              int32_t *slack, int32_t extra, cudaStream_t s);
+                              int32_t *slack, int32_t extra, int32_t *wsum, const int32_t *d1, const int32_t *rp,
+                              int32_t h, cudaStream_t s);
 // dst = a[0..na) followed by b[0..nb).
 cudaError_t launch_concat(int32_t *dst, const int32_t *a, int32_t na, const int32_t *b, int32_t nb, cudaStream_t s);
 // st->nA = sum of p.nAc.
@@ -227,6 +234,7 @@ struct PersistLaunch {
     int32_t *dcount;
     int32_t *comb;  // [n] round source list
     int32_t *cand;  // [n] lazy mode: vertices to recompute exactly (class regions)
+    int32_t *wsum;  // [n] lazy mode: ball bounds of the deleted set (dev_weight_pass), zero between rounds
     int32_t ncls, hmax, alpha;
     GridSync *gs;
     PersistStats *ps;

@@ -47,9 +47,10 @@ __global__ void __launch_bounds__(kBlock) k_min_over_list(const int32_t *list, i
     dev_min_over_list(list, count, deg, p);
 }
 __global__ void k_apply_lazy(const int32_t *list, int32_t inner, int32_t total, int32_t *dcount, int32_t *deg,
-                             int32_t *slack, int32_t extra)
+                             int32_t *slack, int32_t extra, int32_t *wsum, const int32_t *d1, const int32_t *rp,
+                             int32_t h)
 {
-    dev_apply_lazy(list, inner, total, dcount, deg, slack, extra);
+    dev_apply_lazy(list, inner, total, dcount, deg, slack, extra, wsum, d1, rp, h);
 }
 __global__ void k_concat(int32_t *dst, const int32_t *a, int32_t na, const int32_t *b, int32_t nb)
 {
@@ -146,11 +147,12 @@ cudaError_t launch_min_over_list(const int32_t *list, int32_t count, const int32
 }
 
 cudaError_t launch_apply_lazy(const int32_t *list, int32_t inner, int32_t total, int32_t *dcount, int32_t *deg,
-                              int32_t *slack, int32_t extra, cudaStream_t s)
+                              int32_t *slack, int32_t extra, int32_t *wsum, const int32_t *d1, const int32_t *rp,
+                              int32_t h, cudaStream_t s)
 {
     if (total <= 0) return cudaSuccess;
     const int blocks = (total + 511) / 512 < 2048 ? (total + 511) / 512 : 2048;
-    k_apply_lazy<<<blocks, 512, 0, s>>>(list, inner, total, dcount, deg, slack, extra);
+    k_apply_lazy<<<blocks, 512, 0, s>>>(list, inner, total, dcount, deg, slack, extra, wsum, d1, rp, h);
     return cudaGetLastError();
 }
 

@@ -88,6 +88,7 @@ struct PersistArgs {
     int32_t *dcount;     // per vertex: deleted vertices within h
     int32_t *comb;       // round source list: inner vertices, then deleted ones
     int32_t *cand;       // lazy mode: exact-recompute list (class regions)
+    int32_t *wsum;       // lazy mode: ball bounds of the deleted set
     int32_t ncls, hmax, alpha;
     GridSync *gs;
     PersistStats *ps;
@@ -98,11 +99,13 @@ struct PersistArgs {
 // block taking part; phases separated by barriers. Returns false on timeout.
 template <int W>
 __device__ bool bfs_batch(const PersistArgs &a, const int32_t *src, int32_t ns, int32_t h, int32_t *rowcnt,
-                          int32_t row_first)
+                          int32_t row_first, bool weights)
 {
     BfsBufs b = a.b;
     b.rowcnt = rowcnt;
     b.row_first = row_first;
+    b.wsum = weights ? a.wsum : nullptr;
+    b.wdeg = a.deg;
     LevelCtl *ctl = b.ctl;
     // reset the level ring and place the sources (level 0)
     if (!grid_sync(a.gs, a.timeout_ns, [&] {
@@ -154,6 +157,10 @@ __device__ bool bfs_batch(const PersistArgs &a, const int32_t *src, int32_t ns, 
             dev_post<W, true>(a.g, b, lvl, tune);
         else
             dev_post<W, false>(a.g, b, lvl, tune);
+        if (b.wsum && (lvl == h - 2 || lvl == h - 3)) {
+            if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return false;
+            dev_weight_pass<W>(b, src, a.g.row_ptr, a.alive, lvl == h - 2);
+        }
     }
     if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return false;
     dev_end<W>(b, src, ns, a.deg);
@@ -163,12 +170,12 @@ __device__ bool bfs_batch(const PersistArgs &a, const int32_t *src, int32_t ns, 
 // h-degrees of src[0..ns) in batches of 64*W sources.
 template <int W>
 __device__ bool bfs_sources(const PersistArgs &a, const int32_t *src, int32_t ns, int32_t h, int32_t *rowcnt,
-                            int32_t row_first)
+                            int32_t row_first, bool weights = false)
 {
     constexpr int32_t S = 64 * W;
     for (int32_t off = 0; off < ns; off += S) {
         const int32_t cur = ns - off < S ? ns - off : S;
-        if (!bfs_batch<W>(a, src + off, cur, h, rowcnt, row_first > off ? row_first - off : 0)) return false;
+        if (!bfs_batch<W>(a, src + off, cur, h, rowcnt, row_first > off ? row_first - off : 0, weights)) return false;
         if (blockIdx.x == 0 && threadIdx.x == 0) a.ps->source_batches++;
     }
     return true;
@@ -236,10 +243,12 @@ __global__ void __launch_bounds__(kBlock, (W <= 4 ? 2 : 1)) k_decompose(PersistA
             int32_t *Ac = a.A + a.cls_off[c];
             if (a.p.slack) {
                 // lazy mode: row counts of the deleted set, bounds for the rest
-                if (!single && nd > 0 && !bfs_sources<W>(a, a.dcls + a.cls_off[c], nd, a.cls_h[c], a.dcount, 0))
+                if (!single && nd > 0 &&
+                    !bfs_sources<W>(a, a.dcls + a.cls_off[c], nd, a.cls_h[c], a.dcount, 0, true))
                     return;
                 if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
-                dev_apply_lazy(Ac, ni, na, single ? nullptr : a.dcount, a.deg, a.p.slack, ni + nd);
+                dev_apply_lazy(Ac, ni, na, single ? nullptr : a.dcount, a.deg, a.p.slack, ni + nd, a.wsum,
+                               a.dcls + a.cls_off[c], a.g.row_ptr, a.cls_h[c]);
                 continue;
             }
             const bool count_d = na > ni && !single;
@@ -289,6 +298,7 @@ cudaError_t persist_launch_w(const PersistLaunch &L, int grid, cudaStream_t s)
     a.dcount = L.dcount;
     a.comb = L.comb;
     a.cand = L.cand;
+    a.wsum = L.wsum;
     a.ncls = L.ncls;
     a.hmax = L.hmax;
     a.alpha = L.alpha;
