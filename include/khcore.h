@@ -89,6 +89,12 @@ typedef struct {
                                   round loop: the one kernel's duration) */
     double round_bytes;        /* algorithmic bytes of the BFS levels run in the
                                   rounds (same per-level formula) */
+    /* Persistent round loop only (zero otherwise): time between the grid
+     * barriers that close each phase, summed over rounds, as seen by block 0:
+     * [0] level (minimum, bound check), [1] exact recomputes of the lazy mode,
+     * [2] peel-set compaction, [3] affected-set BFS, [4] h-degree update. */
+    double phase_ms[5];
+    int64_t grid_barriers;     /* grid-wide barriers the persistent kernel passed */
 } khcore_stats;
 
 /*

@@ -53,10 +53,13 @@ class Stats(ctypes.Structure):
                 ("edges_traversed", ctypes.c_int64), ("level_launches", ctypes.c_int64),
                 ("level_ms", ctypes.c_double), ("level_bytes", ctypes.c_double),
                 ("recomputed_total", ctypes.c_int64), ("init_ms", ctypes.c_double),
-                ("round_ms", ctypes.c_double), ("round_bytes", ctypes.c_double)]
+                ("round_ms", ctypes.c_double), ("round_bytes", ctypes.c_double),
+                ("phase_ms", ctypes.c_double * 5), ("grid_barriers", ctypes.c_int64)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        out = {k: getattr(self, k) for k, _ in self._fields_}
+        out["phase_ms"] = list(out["phase_ms"])
+        return out
 
 
 _lib = None

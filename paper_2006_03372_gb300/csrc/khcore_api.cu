@@ -702,6 +702,8 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         stt.recomputed_total += psh.recomputed_total;
         stt.deleted_total += psh.deleted_total;
         stt.affected_total += psh.affected_total;
+        for (int k = 0; k < 5; k++) stt.phase_ms[k] = (double)psh.phase_ns[k] * 1e-6;
+        stt.grid_barriers = (int64_t)gsh.passed;
         return finish_decompose(c, G, core_out, round_out, stats, stt, true);
     }
 

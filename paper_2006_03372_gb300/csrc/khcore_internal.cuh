@@ -203,6 +203,7 @@ struct GridSync {
     unsigned gen;
     int err;
     int pad;
+    unsigned long long passed;  // barriers completed
 };
 
 // Statistics the persistent kernel accumulates (zero before the launch).
@@ -214,6 +215,7 @@ struct PersistStats {
     long long affected_total;
     long long level_steps;  // BFS level phases run
     double level_bytes;     // their algorithmic bytes (4 n_b + 4 m_b + 16 W n_b each)
+    unsigned long long phase_ns[5];  // per phase, block 0's time between closing barriers
 };
 
 // Everything the persistent kernel works on (device pointers).

@@ -47,6 +47,7 @@ __device__ __forceinline__ bool grid_sync(GridSync *gs, unsigned long long timeo
         if (arrived == gridDim.x - 1) {
             __threadfence();
             serial();
+            gs->passed++;
             gs->count = 0;
             __threadfence();
             atomicAdd(&gs->gen, 1u);
@@ -184,19 +185,32 @@ __device__ bool bfs_sources(const PersistArgs &a, const int32_t *src, int32_t ns
 template <int W>
 __global__ void __launch_bounds__(kBlock, (W <= 4 ? 2 : 1)) k_decompose(PersistArgs a)
 {
+    // phase clock of block 0: called right after a barrier, so the phase
+    // before it is complete on every block
+    unsigned long long t_last = (blockIdx.x == 0 && threadIdx.x == 0) ? global_ns() : 0;
+    auto mark = [&](int ph) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            const unsigned long long t = global_ns();
+            a.ps->phase_ns[ph] += t - t_last;
+            t_last = t;
+        }
+    };
     // the initial h-degrees are in deg already (computed by the per-phase
     // kernels at the widest W); the rounds follow
     for (;;) {
         // level of every graph: k_g <- max(k_g, min alive h-degree)
         if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
+        mark(4);
         dev_min_alive_deg(a.g.n, a.alive, a.deg, a.p);
         if (a.p.slack) {
             // lazy mode: exact recompute of the vertices whose bounds leave
             // their fate at the coming level open
             if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
             dev_refine_select(a.g.n, a.alive, a.deg, a.p, a.cand);
+            if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
+            mark(0);
             for (int32_t c = 0; c < a.ncls; c++) {
-                if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
+                if (c > 0 && !grid_sync(a.gs, a.timeout_ns, Nop{})) return;
                 const int32_t nc = *((volatile int32_t *)&a.p.ncand[c]);
                 if (nc <= 0) continue;
                 const int32_t *cl = a.cand + a.cls_off[c];
@@ -207,9 +221,11 @@ __global__ void __launch_bounds__(kBlock, (W <= 4 ? 2 : 1)) k_decompose(PersistA
             }
         }
         if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
+        mark(a.p.slack ? 1 : 0);
         dev_set_level(a.p, a.st);
         // peel set D
         if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
+        mark(0);
         dev_peel_compact(a.g.n, a.g.row_ptr, a.alive, a.deg, a.p, a.st, a.core, a.rnd, a.vis, a.aq[0], a.dcls);
         // affected set A: BFS from D through survivors; snapshot the per-class
         // counts before the level that reaches distance h of each class
@@ -219,6 +235,7 @@ __global__ void __launch_bounds__(kBlock, (W <= 4 ? 2 : 1)) k_decompose(PersistA
                         if (a.cls_h[c] == lvl + 1) a.inner[c] = a.p.nAc[c];
                 }))
                 return;
+            mark(lvl == 0 ? 2 : 3);
             dev_affected_push(a.g, a.alive, lvl, a.aq[0], a.aq[1], a.aq[2], a.vis, a.p, a.st, a.A, lvl == a.hmax - 1);
         }
         if (!grid_sync(a.gs, a.timeout_ns, [&] {
@@ -230,6 +247,7 @@ __global__ void __launch_bounds__(kBlock, (W <= 4 ? 2 : 1)) k_decompose(PersistA
                 a.ps->affected_total += s;
             }))
             return;
+        mark(3);
         const int32_t alive_left = *((volatile int32_t *)&a.st->alive);
         if (alive_left == 0) break;
         const bool single = *((volatile int32_t *)&a.st->nD) == 1;
