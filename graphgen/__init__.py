@@ -392,10 +392,17 @@ def cached(key: str, make) -> Graph:
     return g
 
 
+def profile_chung_lu() -> Graph:
+    """The 1M Chung-Lu recipe at n=2e5 (same mean degree, exponent, cap and
+    seed): a smaller case of the same kernels for counter captures."""
+    return config2_chung_lu(200_000)
+
+
 CONFIGS = {
     "er2000": (config1_er, (2,)),
     "cl1m": (config2_chung_lu, (2, 3)),
     "rmat18": (config3_rmat, (4, 5)),
+    "cl200k": (profile_chung_lu, (2,)),
 }
 
 
