@@ -137,6 +137,49 @@ khcore_status khcore_hdegrees_of(khcore_ctx *ctx, int32_t h, int32_t count, cons
                                  int32_t *deg_out);
 
 /*
+ * khcore_hdegrees_static — the h-degrees of khcore_hdegrees_of without any
+ * device allocation and without a context. The paper has no counterpart.
+ *
+ * For callers that may not allocate device memory while they run: a plugin
+ * inside a host process that owns all device memory through its own pool and
+ * hands it only input and output buffers, or a latency-bound path that cannot
+ * take cudaMalloc's device-wide synchronisation. The BFS scratch comes from a
+ * fixed 32 MiB array in the library's device image, which every device that
+ * loads the library holds until the process exits. This call allocates
+ * nothing (no cudaMalloc, cudaFree or allocating library routine); it only
+ * copies four status words to a host stack buffer and synchronises `stream`
+ * once after its checks and once before returning.
+ *
+ *   n, m     vertices and CSR entries of the graph (m = row_ptr[n])
+ *   row_ptr  int32[n+1], device: CSR offsets, row_ptr[0] = 0, non-decreasing
+ *   col      int32[m], device: neighbour ids in [0, n). Self-loops, repeated
+ *            entries and one-way edges are not detected here: the caller
+ *            passes the same symmetric simple graph khcore_create accepts
+ *   h        hop bound, h >= 1; h > n-1 acts as n-1
+ *   count    number of listed vertices, 0 <= count <= n
+ *   verts    int32[count], device: distinct ids in [0, n)
+ *   deg_out  int32[count], device: deg_out[i] = d^h of verts[i] in G
+ *   stream   cudaStream_t the work is ordered on (NULL: the legacy default
+ *            stream)
+ * Limit: the scratch needs about 74 n + 0.2 m bytes (exactly: 256-byte
+ * aligned regions of the multi-source BFS at 64 sources per batch); larger
+ * graphs are rejected with KHCORE_EINVAL and a message naming the bytes
+ * needed, before any device work. Offsets that are not a CSR, ids out of
+ * range and repeated listed ids are found on the device and also return
+ * KHCORE_EINVAL. Messages: khcore_last_error(NULL), per host thread.
+ * Set-up: the first call on a device, with that device current, looks up
+ * the array's device address (cudaGetSymbolAddress) and caches it; make that
+ * first call before any stream capture begins.
+ * Sharing: every call on a device uses the same array, and each call clears
+ * the parts that must start at zero. Calls whose device work overlaps (two
+ * host threads, or two streams, on one device) race on the array and give
+ * wrong results: order them, e.g. on one stream from one thread.
+ */
+khcore_status khcore_hdegrees_static(int32_t n, int64_t m, const int32_t *row_ptr, const int32_t *col,
+                                     int32_t h, int32_t count, const int32_t *verts, int32_t *deg_out,
+                                     void *stream);
+
+/*
  * khcore_decompose — core_h(v) for every vertex (problem statement, Sec. II).
  *   h         hop bound, h >= 1 (EINVAL otherwise); h > n-1 acts as n-1
  *   core_out  int32[n], host or device

@@ -31,7 +31,7 @@ __all__ = [
     "khcore_set_push_alpha", "khcore_set_round_loop", "khcore_set_wait_limit", "khcore_set_round_words", "khcore_set_lazy",
     "khcore_status_string", "Stats",
     "KHCore", "library_path", "load_library", "khcore_batch_create", "khcore_batch_decompose", "pack_graphs",
-    "khcore_hdegrees_of", "Server", "request_bytes",
+    "khcore_hdegrees_of", "khcore_hdegrees_static", "Server", "request_bytes",
 ]
 
 STATUS = {0: "KHCORE_OK", 1: "KHCORE_EINVAL", 2: "KHCORE_ENOMEM", 3: "KHCORE_ECUDA",
@@ -118,6 +118,8 @@ def load_library(build_if_missing: bool = False):
         lib.khcore_num_entries.restype = i64
         lib.khcore_hdegrees_of.argtypes = [P, i32, i32, P, P]
         lib.khcore_hdegrees_of.restype = ctypes.c_int
+        lib.khcore_hdegrees_static.argtypes = [i32, i64, P, P, i32, i32, P, P, P]
+        lib.khcore_hdegrees_static.restype = ctypes.c_int
         sz = ctypes.c_size_t
         lib.khcore_request_bytes.argtypes = [i32, i64]
         lib.khcore_request_bytes.restype = sz
@@ -275,6 +277,32 @@ def khcore_hdegrees_of(ctx, h: int, verts, deg_out=None):
     _check(lib, ctx, lib.khcore_hdegrees_of(ctx, int(h), int(count), pv, po))
     del k
     return out
+
+
+def khcore_hdegrees_static(n: int, m: int, row_ptr, col, h: int, verts, deg_out, stream=None):
+    """d_v^h(G) of the listed vertices with no device allocation.
+
+    For callers that may not allocate device memory while they run (a plugin
+    whose host process owns all device memory, a latency-bound path). Every
+    array is a CUDA int32 tensor the caller already holds: row_ptr [n+1],
+    col [m], verts [count] (distinct ids), deg_out [count]. The scratch is a
+    fixed array inside the library, shared by every call on a device: calls
+    whose device work overlaps race, so order them on one stream."""
+    lib = load_library()
+    for a in (row_ptr, col, verts, deg_out):
+        if not (_is_torch(a) and a.is_cuda):
+            raise TypeError("khcore_hdegrees_static takes CUDA int32 tensors only")
+    if len(deg_out) != len(verts):
+        raise ValueError("deg_out and verts differ in length")
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    prp, _ = _ptr(row_ptr)
+    pcl, _ = _ptr(col)
+    pv, _ = _ptr(verts)
+    po, _ = _ptr(deg_out)
+    _check(lib, None, lib.khcore_hdegrees_static(int(n), int(m), prp, pcl, int(h), int(len(verts)), pv, po,
+                                                 ctypes.c_void_p(stream) if stream else None))
+    return deg_out
 
 
 def khcore_decompose(ctx, h: int, core_out=None):

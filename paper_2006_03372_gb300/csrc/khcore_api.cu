@@ -831,6 +831,23 @@ khcore_status create_common(int32_t G, const std::vector<int64_t> &v_off, std::v
 
 }  // namespace
 
+namespace khc {
+
+// Failure message for khcore_last_error(NULL), for the entry points that take
+// no context.
+khcore_status set_thread_error(khcore_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_create_err = buf;
+    return s;
+}
+
+}  // namespace khc
+
 
 extern "C" {
 
