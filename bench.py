@@ -53,6 +53,8 @@ def parse():
                    help="decompose: the headline (default); batch: many graphs per launch vs one graph "
                         "per launch; serve: open-loop request server")
     p.add_argument("--graphs", type=int, default=1024, help="batch workload: first k of the 1024 graphs")
+    p.add_argument("--solo-graphs", type=int, default=64,
+                   help="batch workload: graphs timed one per launch (a size-stratified sample; 0 = all)")
     p.add_argument("--serve-seconds", type=float, default=60.0, help="serve workload: arrival window")
     p.add_argument("--serve-rate", type=float, default=200.0, help="serve workload: requests per second")
     p.add_argument("--serve-max-n", type=int, default=500_000, help="serve workload: largest request n")
@@ -122,6 +124,10 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ helpers
+
+def workload_name(args, g) -> str:
+    return WORKLOAD if args.graph == "cl1m" else f"{args.graph}:{g.name}"
+
 
 def load_peaks():
     try:
@@ -236,7 +242,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * len(hs) / value,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "hs": hs, "n": g.n, "m": g.m},
+        "data": "synthetic", "config": {"workload": workload_name(args, g), "hs": hs, "n": g.n, "m": g.m},
         "cpu_baseline": dict(last, value=value),
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": wall,
@@ -352,7 +358,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": g.n, "m": g.m, "hs": hs,
+        "config": {"workload": workload_name(args, g), "n": g.n, "m": g.m, "hs": hs,
                    "words_per_vertex": stats[-1]["words_per_vertex"],
                    "l2": "2x-L2 buffer written before every decomposition; working set > L2",
                    "parallelism": f"replicas{world}"},
@@ -400,11 +406,16 @@ def run_batch(args):
     _, _, st = kh.khcore_batch_decompose(ctx, h, core, want_rounds=False)
     t_batch = time.perf_counter() - t0
     kh.khcore_destroy(ctx)
-    # one graph per launch sequence
+    # one graph per launch sequence, on every graph or on a sample stratified
+    # by size (every (G/k)-th graph in size order)
+    sizes = np.diff(v_off)
+    by_size = np.argsort(sizes, kind="stable")
+    k = G if args.solo_graphs <= 0 or args.solo_graphs >= G else args.solo_graphs
+    solo_idx = by_size[np.linspace(0, G - 1, k).round().astype(np.int64)] if k < G else np.arange(G)
     t_solo = 0.0
     same = True
-    for i in range(G):
-        g = gg.unpack(v_off, e_off, rp, col, i)
+    for i in solo_idx:
+        g = gg.unpack(v_off, e_off, rp, col, int(i))
         c = kh.khcore_create(g.n, g.row_ptr, g.col, kh.FLAG_TRUST_INPUT)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -412,9 +423,13 @@ def run_batch(args):
         t_solo += time.perf_counter() - t0
         kh.khcore_destroy(c)
         same &= bool((out == core[v_off[i]:v_off[i + 1]]).all())
+    solo_rate = len(solo_idx) / t_solo
     line = {"workload": "batch", "graphs": G, "vertices": int(v_off[-1]), "entries": int(e_off[-1]),
-            "batched_graphs_per_s": G / t_batch, "one_per_launch_graphs_per_s": G / t_solo,
-            "speedup": t_solo / t_batch, "batched_s": t_batch, "one_per_launch_s": t_solo,
+            "batched_graphs_per_s": G / t_batch, "one_per_launch_graphs_per_s": solo_rate,
+            "speedup": (G / t_batch) / solo_rate, "batched_s": t_batch,
+            "one_per_launch_s": t_solo, "one_per_launch_graphs": int(len(solo_idx)),
+            "one_per_launch_sample": "all graphs" if k == G else f"{k} graphs, every (G/{k})-th in size order",
+            "batched_path": "one block per graph" if st["words_per_vertex"] == 1 else "grid-wide rounds",
             "rounds": st["rounds"], "identical_to_solo": same,
             "h_counts": {str(k): int((h == k).sum()) for k in (2, 3, 4)}}
     print(json.dumps(line), flush=True)

@@ -289,6 +289,19 @@ khcore_status khcore_set_lazy(khcore_ctx *ctx, int32_t on);
 khcore_status khcore_set_round_loop(khcore_ctx *ctx, int32_t mode);
 
 /*
+ * khcore_set_graph_blocks — for contexts of many small graphs: one thread
+ * block decomposes each whole graph (initial h-degrees and every round), the
+ * blocks taking graphs largest first, with no grid-wide barrier and no host
+ * round trip; the grid stays busy with other graphs while one graph runs its
+ * rounds. mode 0 (default): used when the context holds at least 64 graphs
+ * and none has more than 8,192 vertices; 1: always; -1: never. Results
+ * are identical either way (the per-block path recomputes the inner affected
+ * vertices eagerly; khcore_set_lazy and khcore_set_round_loop do not apply
+ * to it). EINVAL for other modes.
+ */
+khcore_status khcore_set_graph_blocks(khcore_ctx *ctx, int32_t mode);
+
+/*
  * khcore_set_wait_limit — time limit of one grid-barrier wait of the
  * persistent kernel, in nanoseconds (default 10 s). A wait that runs out stops
  * the decomposition with KHCORE_ETIMEOUT; the context stays usable and the

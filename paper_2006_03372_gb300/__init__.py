@@ -28,7 +28,7 @@ from ._build import build as _build_lib
 __all__ = [
     "KHCoreError", "khcore_create", "khcore_hdegrees", "khcore_decompose", "khcore_decompose_ex",
     "khcore_destroy", "khcore_last_error", "khcore_set_words", "khcore_set_profiling",
-    "khcore_set_push_alpha", "khcore_set_round_loop", "khcore_set_wait_limit", "khcore_set_round_words", "khcore_set_lazy",
+    "khcore_set_push_alpha", "khcore_set_round_loop", "khcore_set_wait_limit", "khcore_set_round_words", "khcore_set_lazy", "khcore_set_graph_blocks",
     "khcore_status_string", "Stats",
     "KHCore", "library_path", "load_library", "khcore_batch_create", "khcore_batch_decompose", "pack_graphs",
     "khcore_hdegrees_of", "khcore_hdegrees_static", "Server", "request_bytes",
@@ -106,6 +106,8 @@ def load_library(build_if_missing: bool = False):
         lib.khcore_set_push_alpha.restype = ctypes.c_int
         lib.khcore_set_lazy.argtypes = [P, i32]
         lib.khcore_set_lazy.restype = ctypes.c_int
+        lib.khcore_set_graph_blocks.argtypes = [P, i32]
+        lib.khcore_set_graph_blocks.restype = ctypes.c_int
         lib.khcore_set_round_loop.argtypes = [P, i32]
         lib.khcore_set_round_loop.restype = ctypes.c_int
         lib.khcore_set_wait_limit.argtypes = [P, ctypes.c_uint64]
@@ -229,6 +231,12 @@ def khcore_set_lazy(ctx, on: int) -> None:
     """1 (default): bound-based exact peeling; 0: recompute every inner affected vertex."""
     lib = load_library()
     _check(lib, ctx, lib.khcore_set_lazy(ctx, int(on)))
+
+
+def khcore_set_graph_blocks(ctx, mode: int) -> None:
+    """0: automatic; 1: one thread block per whole graph; -1: grid-wide rounds only."""
+    lib = load_library()
+    _check(lib, ctx, lib.khcore_set_graph_blocks(ctx, int(mode)))
 
 
 def khcore_set_round_loop(ctx, mode: int) -> None:
@@ -440,11 +448,13 @@ class KHCore:
     """Context manager around one device-resident graph."""
 
     def __init__(self, n, row_ptr, col, flags: int = 0, stream=None, words: int = 0, alpha=None, loop=None,
-                 lazy=None):
+                 lazy=None, blocks=None):
         self.ctx = khcore_create(n, row_ptr, col, flags, stream)
         self.n = int(n)
         if lazy is not None:
             khcore_set_lazy(self.ctx, lazy)
+        if blocks is not None:
+            khcore_set_graph_blocks(self.ctx, blocks)
         if loop is not None:
             khcore_set_round_loop(self.ctx, loop)
         if words:

@@ -72,6 +72,11 @@ struct khcore_ctx {
     unsigned long long *alg = nullptr;    // device counter of algorithmic bytes of the BFS levels
     int32_t push_alpha = 16;              // push when frontier degree sum * alpha < alive CSR entries
     int32_t round_loop = 0;               // 0: one persistent launch per decomposition, 1: host-driven rounds
+    int32_t graph_blocks = 0;             // 0: auto, 1: one thread block per graph, -1: never
+    int32_t *voff_d = nullptr;            // [G+1] vertex offsets (int32) for the per-block path
+    int32_t *order_d = nullptr;           // [G] graph order of the per-block path
+    int32_t *bnext = nullptr;             // per-block path work counter
+    BlockStats *bstats = nullptr;
     unsigned long long wait_limit_ns = 10ull * 1000 * 1000 * 1000;  // one grid-barrier wait
     bool dirty = false;                   // a launch stopped midway: BFS buffers need clearing
     int32_t *cls_size = nullptr;          // [G] initial class sizes (device)
@@ -455,7 +460,16 @@ khcore_status setup_ctx(khcore_ctx *c, const std::vector<int32_t> &rp, const std
     A(dev_alloc(&c->gs, 1));
     A(dev_alloc(&c->pstats, 1));
     if (c->G > 1) A(dev_alloc(&c->gid, (size_t)n));
+    A(dev_alloc(&c->voff_d, (size_t)c->G + 1));
+    A(dev_alloc(&c->order_d, (size_t)c->G));
+    A(dev_alloc(&c->bnext, 1));
+    A(dev_alloc(&c->bstats, 1));
     if (st != KHCORE_OK) return st;
+    {
+        std::vector<int32_t> vo(c->v_off.begin(), c->v_off.end());
+        e = cudaMemcpy(c->voff_d, vo.data(), sizeof(int32_t) * vo.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(nullptr, KHCORE_ECUDA, "offset upload: %s", cudaGetErrorString(e));
+    }
     e = cudaMallocHost((void **)&c->st_host, sizeof(PeelState));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->nAc_host, 4 * sizeof(int32_t) * (size_t)c->G);
     if (e == cudaSuccess && n) e = cudaMemsetAsync(c->dcount, 0, sizeof(int32_t) * (size_t)n, c->stream);
@@ -620,6 +634,65 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
     stt.kernel_launches += 1;
     // the host vectors above must outlive the async copies
     CU(cudaStreamSynchronize(c->stream));
+
+    // Many small graphs: one thread block decomposes each whole graph, with no
+    // grid-wide barrier (khcore_block.cu).
+    int32_t nmax = 0;
+    for (int32_t gi = 0; gi < G; gi++) nmax = std::max<int32_t>(nmax, (int32_t)(c->v_off[gi + 1] - c->v_off[gi]));
+    const bool blocks = c->graph_blocks > 0 || (c->graph_blocks == 0 && G >= kBlockGraphsMinCount &&
+                                                nmax <= kBlockGraphsMaxN);
+    if (blocks) {
+        std::vector<int32_t> order(G);
+        for (int32_t gi = 0; gi < G; gi++) order[gi] = gi;
+        std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+            return c->v_off[x + 1] - c->v_off[x] > c->v_off[y + 1] - c->v_off[y];
+        });
+        CU(cudaMemcpyAsync(c->order_d, order.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, c->stream));
+        CU(cudaMemsetAsync(c->bnext, 0, sizeof(int32_t), c->stream));
+        CU(cudaMemsetAsync(c->bstats, 0, sizeof(BlockStats), c->stream));
+        CU(cudaEventRecord(c->ev_init, c->stream));
+        BlockLaunch L;
+        L.rp = c->row_ptr;
+        L.col = c->col;
+        L.voff = c->voff_d;
+        L.hg = c->hg;
+        L.order = c->order_d;
+        L.count = G;
+        L.next = c->bnext;
+        L.alive = c->alive;
+        L.deg = c->deg;
+        L.core = c->core;
+        L.rnd = c->rnd;
+        L.kg = c->kg;
+        L.V = c->V;
+        L.F0 = c->F[0];
+        L.F1 = c->F[1];
+        L.live0 = c->src;
+        L.live1 = c->comb;
+        L.qa = c->Q[0];
+        L.qb = c->Q[1];
+        L.tl = c->T;
+        L.al = c->Q[2];
+        L.dl = c->dcls;
+        L.sl = c->cand;
+        L.mark = c->slack;  // zero here (cleared above) and left zero
+        L.dcount = c->dcount;
+        L.edges = c->edges;
+        L.bs = c->bstats;
+        const int bgrid = std::min(G, c->sm_count * max_blocks_per_sm_block_decompose());
+        CU(launch_decompose_blocks(L, bgrid, c->stream));
+        BlockStats bsh;
+        CU(cudaMemcpyAsync(&bsh, c->bstats, sizeof bsh, cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        stt.kernel_launches += 1;
+        stt.words_per_vertex = 1;
+        stt.rounds = (int32_t)bsh.rounds;
+        stt.source_batches += bsh.batches;
+        stt.affected_total += bsh.affected;
+        stt.recomputed_total += bsh.recomputed;
+        stt.deleted_total += c->n;
+        return finish_decompose(c, G, core_out, round_out, stats, stt, true);
+    }
 
     // initial h-degrees, class by class
     for (int32_t k = 0; k < ncls; k++)
@@ -848,7 +921,6 @@ khcore_status set_thread_error(khcore_status s, const char *fmt, ...)
 
 }  // namespace khc
 
-
 extern "C" {
 
 const char *khcore_status_string(khcore_status s)
@@ -877,7 +949,7 @@ void khcore_destroy(khcore_ctx *c)
     cudaSetDevice(c->device);
     if (c->stream && !c->failed) cudaStreamSynchronize(c->stream);
     void *bufs[] = {c->row_ptr, c->col, c->classes, c->gid, c->kg, c->ming, c->hg, c->gcls, c->cls_off, c->nAc,
-                    c->nDc, c->inner, c->clsh, c->dcls, c->dcount, c->comb, c->slack, c->wsum, c->cand, c->mind, c->minub, c->ncand, c->cls_size, c->gs, c->pstats,
+                    c->nDc, c->inner, c->clsh, c->dcls, c->dcount, c->comb, c->slack, c->wsum, c->cand, c->voff_d, c->order_d, c->bnext, c->bstats, c->mind, c->minub, c->ncand, c->cls_size, c->gs, c->pstats,
                     c->cls_src, c->alive, c->deg, c->core, c->rnd, c->src, c->vis, c->st, c->V, c->F[0], c->F[1],
                     c->flag[0], c->flag[1], c->Q[0], c->Q[1], c->Q[2], c->I[0], c->I[1], c->I[2], c->T, c->ctl,
                     c->cnt, c->edges, c->alg};
@@ -1006,6 +1078,14 @@ khcore_status khcore_set_round_loop(khcore_ctx *c, int32_t mode)
     if (!c) return KHCORE_EINVAL;
     if (mode != 0 && mode != 1) return fail(c, KHCORE_EINVAL, "mode must be 0 (device) or 1 (host), got %d", mode);
     c->round_loop = mode;
+    return KHCORE_OK;
+}
+
+khcore_status khcore_set_graph_blocks(khcore_ctx *c, int32_t mode)
+{
+    if (!c) return KHCORE_EINVAL;
+    if (mode < -1 || mode > 1) return fail(c, KHCORE_EINVAL, "mode must be -1, 0 or 1, got %d", mode);
+    c->graph_blocks = mode;
     return KHCORE_OK;
 }
 

@@ -243,6 +243,40 @@ struct PersistLaunch {
     unsigned long long timeout_ns;  // limit of one barrier wait
 };
 
+// Whole decompositions of small graphs, one thread block per graph
+// (khcore_block.cu). Union-indexed arrays; each block touches only the vertex
+// range of the graph it works on. V, F0, F1 (one 64-bit row per vertex),
+// mark and dcount are zero on entry and on exit; the list arrays (n entries
+// each) are scratch.
+// Automatic choice of the per-block path: at least this many graphs, none
+// larger than this many vertices.
+constexpr int32_t kBlockGraphsMinCount = 64;
+constexpr int32_t kBlockGraphsMaxN = 1 << 13;
+struct BlockStats {
+    long long rounds;      // largest per-graph round count
+    long long batches;     // BFS batches of 64 sources
+    long long affected;    // sum of |A| over rounds and graphs
+    long long recomputed;  // sum of the inner parts recomputed by BFS
+};
+struct BlockLaunch {
+    const int32_t *rp, *col;
+    const int32_t *voff;   // [G+1] vertex offsets
+    const int32_t *hg;     // [G] effective h
+    const int32_t *order;  // graphs to decompose, in the order they are taken
+    int32_t count;         // entries of order
+    int32_t *next;         // work counter, zero before the launch
+    uint32_t *alive;       // all bits of the listed graphs set on entry
+    int32_t *deg, *core, *rnd, *kg;
+    uint64_t *V, *F0, *F1;
+    int32_t *live0, *live1, *qa, *qb, *tl, *al, *dl, *sl;
+    int32_t *mark, *dcount;
+    unsigned long long *edges;
+    BlockStats *bs;
+};
+cudaError_t launch_decompose_blocks(const BlockLaunch &L, int grid, cudaStream_t s);
+int max_blocks_per_sm_block_decompose();
+int block_decompose_threads();
+
 // Cooperative launch of the whole decomposition; grid must not exceed
 // max_blocks_per_sm_persist(W) * SMs.
 cudaError_t launch_decompose_persist(int W, const PersistLaunch &L, int grid, cudaStream_t s);

@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/khcore.h"
+#include "khcore_internal.cuh"
 
 namespace {
 
@@ -69,7 +70,9 @@ namespace {
 // (3 arrays of W 64-bit words per vertex, W <= 16).
 size_t request_bytes(int32_t n, int64_t m) { return (size_t)n * (64 + 3 * 8 * 16) + (size_t)m * 4 + 4096; }
 
-void run_batch(khcore_server *s, std::vector<Request *> &batch, cudaStream_t stream)
+// One batch context over the group; blocks: one thread block per graph (all
+// graphs small) instead of grid-wide rounds.
+void run_group(khcore_server *s, std::vector<Request *> &batch, cudaStream_t stream, bool blocks)
 {
     const int32_t G = (int32_t)batch.size();
     std::vector<int64_t> v_off(G + 1, 0), e_off(G + 1, 0);
@@ -88,9 +91,12 @@ void run_batch(khcore_server *s, std::vector<Request *> &batch, cudaStream_t str
     khcore_status st = khcore_batch_create(G, v_off.data(), e_off.data(), rp.data(), col.empty() ? nullptr : col.data(),
                                            KHCORE_FLAG_TRUST_INPUT, stream, &ctx);
     std::string msg;
-    // host-driven rounds: the small kernels of concurrent batches interleave
-    // on the device, where a persistent kernel would hold every SM
-    if (st == KHCORE_OK) st = khcore_set_round_loop(ctx, 1);
+    // small graphs: one block each (no grid barrier, so concurrent groups
+    // interleave freely); large graphs: host-driven rounds, whose small
+    // kernels interleave with other groups where a persistent kernel would
+    // hold every SM
+    if (st == KHCORE_OK) st = khcore_set_graph_blocks(ctx, blocks ? 1 : -1);
+    if (st == KHCORE_OK && !blocks) st = khcore_set_round_loop(ctx, 1);
     if (st == KHCORE_OK) {
         st = khcore_batch_decompose(ctx, h.data(), core.data(), nullptr, nullptr);
         if (st != KHCORE_OK) msg = khcore_last_error(ctx);
@@ -113,6 +119,16 @@ void run_batch(khcore_server *s, std::vector<Request *> &batch, cudaStream_t str
     s->batches++;
     s->cv_done.notify_all();
     s->cv_work.notify_all();  // budget freed
+}
+
+// An admitted group: the graphs small enough for one block each run as one
+// per-block batch, the rest as one grid-wide batch.
+void run_batch(khcore_server *s, std::vector<Request *> &batch, cudaStream_t stream)
+{
+    std::vector<Request *> small, large;
+    for (Request *r : batch) (r->n <= khc::kBlockGraphsMaxN ? small : large).push_back(r);
+    if (!small.empty()) run_group(s, small, stream, true);
+    if (!large.empty()) run_group(s, large, stream, false);
 }
 
 void worker_main(khcore_server *s)

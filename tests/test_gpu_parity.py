@@ -247,3 +247,60 @@ def test_lazy_bounds_and_eager_recompute_agree(kh, loop):
             assert (c0 == want).all() and (c1 == want).all(), (g.name, h)
             assert (r0 == r1).all() and s0["rounds"] == s1["rounds"], (g.name, h)
             assert s1["recomputed_total"] <= s0["recomputed_total"] + g.n, (g.name, h)
+
+
+def _batch_graphs(seed, count, nmax):
+    rng = gg.Stream(seed, "block-batch")
+    graphs, hs = [], []
+    for i in range(count):
+        n = int(2 + rng.below(nmax, 1)[0])
+        if i % 4 == 0:
+            graphs.append(gg.erdos_renyi_gnm(n, min(3 * n, n * (n - 1) // 2), 900 + i))
+        elif i % 4 == 1 and n >= 8:
+            graphs.append(gg.chung_lu(n, min(4.0, n / 4), 2.3, max(n / 2, 8.0), 950 + i))
+        elif i % 4 == 2:
+            graphs.append(gg.cycle(n))
+        else:
+            graphs.append(gg.star(n))
+        hs.append(int(1 + rng.below(5, 1)[0]))
+    graphs.append(gg.empty(1))
+    hs.append(3)
+    return graphs, np.array(hs, dtype=np.int32)
+
+
+def test_graph_blocks_batch_matches_solo_oracle_and_grid_path(kh):
+    """A batch of 81 small graphs takes the one-block-per-graph path by
+    default: each graph's core indices equal the oracle's on that graph alone,
+    and cores and rounds equal the grid-wide path's."""
+    graphs, hs = _batch_graphs(81, 80, 150)
+    v_off, e_off, rp, col = kh.pack_graphs(graphs)
+    ctx = kh.khcore_batch_create(v_off, e_off, rp, col)
+    try:
+        out = {}
+        for mode in (0, -1, 1):
+            kh.khcore_set_graph_blocks(ctx, mode)
+            out[mode] = kh.khcore_batch_decompose(ctx, hs)
+        core, rnd, st = out[0]
+        assert st["words_per_vertex"] == 1  # the per-block path ran
+        for g, h, a, b in zip(graphs, hs, v_off[:-1], v_off[1:]):
+            assert (core[a:b] == oracle.peel(g, int(h))).all(), (g.name, h)
+            assert oracle.certificate(g, int(h), core[a:b], rnd[a:b])[0] == 0
+        for mode in (-1, 1):
+            assert (out[mode][0] == core).all() and (out[mode][1] == rnd).all(), mode
+        assert out[-1][2]["rounds"] == st["rounds"]
+    finally:
+        kh.khcore_destroy(ctx)
+
+
+@pytest.mark.parametrize("h", [1, 2, 3, 4, 5])
+def test_graph_blocks_single_graphs(kh, h):
+    """One block decomposing one graph, forced: equal to the oracle, rounds
+    equal to the grid path's; graphs span many 64-source batches."""
+    for g in list(small_graphs(70 + h, 6, (2, 300))) + [gg.chung_lu(700, 6.0, 2.3, 60.0, 71 + h)]:
+        want = oracle.peel(g, h)
+        with kh.KHCore.from_graph(g, blocks=1) as ctx:
+            c, r, st = ctx.decompose_ex(h)
+        with kh.KHCore.from_graph(g, blocks=-1) as ctx:
+            c2, r2, st2 = ctx.decompose_ex(h)
+        assert (c == want).all(), (g.name, h)
+        assert (r == r2).all() and st["rounds"] == st2["rounds"], (g.name, h)
