@@ -49,9 +49,10 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=1, help="end-to-end runs through host buffers (0: skip)")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU work of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", choices=["decompose", "batch", "serve"], default="decompose",
-                   help="decompose: the headline (default); batch: many graphs per launch vs one graph "
-                        "per launch; serve: open-loop request server")
+    p.add_argument("--workload", choices=["decompose", "hdeg", "batch", "serve"], default="decompose",
+                   help="decompose: the headline (default); hdeg: the all-vertex h-degree pass alone "
+                        "(h-hop BFS rate); batch: many graphs per launch vs one graph per launch; serve: "
+                        "open-loop request server")
     p.add_argument("--graphs", type=int, default=1024, help="batch workload: first k of the 1024 graphs")
     p.add_argument("--solo-graphs", type=int, default=64,
                    help="batch workload: graphs timed one per launch (a size-stratified sample; 0 = all)")
@@ -386,6 +387,54 @@ def run_ours(args):
     return 0
 
 
+def run_hdeg(args):
+    """The all-vertex h-degree pass (multi-source h-bounded BFS) alone: the
+    traversed-edges rate and the level kernels' algorithmic bandwidth."""
+    import torch
+
+    import graphgen as gg
+    import paper_2006_03372_gb300 as kh
+    torch.cuda.set_device(0)
+    hs = [int(x) for x in args.hs.split(",")]
+    g = gg.config_graph(args.graph)
+    stream = torch.cuda.current_stream()
+    rp_d = torch.from_numpy(g.row_ptr).cuda()
+    col_d = torch.from_numpy(g.col).cuda()
+    ctx = kh.khcore_create(g.n, rp_d, col_d, kh.FLAG_TRUST_INPUT, stream)
+    if args.words:
+        kh.khcore_set_words(ctx, args.words)
+    kh.khcore_set_profiling(ctx, 1)
+    deg_d = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+    peak, peak_kind = load_peaks()
+    out = {}
+    for h in hs:
+        for _ in range(args.warmup):
+            flush.zero_()
+            kh.khcore_hdegrees_ex(ctx, h, deg_d)
+        sts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            _, st = kh.khcore_hdegrees_ex(ctx, h, deg_d)
+            sts.append(st)
+        ms = sum(s["device_ms"] for s in sts) / len(sts)
+        lvl_ms = sum(s["level_ms"] for s in sts)
+        lvl_n = sum(s["level_launches"] for s in sts)
+        lvl_b = sum(s["level_bytes"] for s in sts)
+        ach = (lvl_b / lvl_n) / (lvl_ms / lvl_n / 1e3) / 1e9 if lvl_ms > 0 else None
+        out[str(h)] = {"pass_ms": ms, "gteps": sts[-1]["edges_traversed"] / (ms / 1e3) / 1e9,
+                       "edges_traversed": sts[-1]["edges_traversed"], "words_per_vertex": sts[-1]["words_per_vertex"],
+                       "source_batches": sts[-1]["source_batches"],
+                       "roofline": {"bound": "hbm", "kernel": "k_level (all levels of the pass)", "achieved": ach,
+                                    "peak": peak, "unit": "GB/s", "frac": ach / peak if ach else None,
+                                    "peak_kind": peak_kind, "level_share": lvl_ms / sum(s["device_ms"] for s in sts)}}
+    kh.khcore_destroy(ctx)
+    line = {"workload": "hdeg", "graph": workload_name(args, g), "n": g.n, "m": g.m, "steps": args.steps,
+            "warmup": args.warmup, "l2": "2x-L2 buffer written before every pass", "per_h": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batch(args):
     """Batched decomposition: all graphs in one context (one launch sequence)
     against one context and decomposition per graph, on the same GPU."""
@@ -475,6 +524,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "hdeg":
+        return run_hdeg(args)
     if args.workload == "batch":
         return run_batch(args)
     if args.workload == "serve":

@@ -126,6 +126,16 @@ khcore_status khcore_create(int32_t n, const int32_t *row_ptr, const int32_t *co
 khcore_status khcore_hdegrees(khcore_ctx *ctx, int32_t h, int32_t *deg_out);
 
 /*
+ * khcore_hdegrees_ex — khcore_hdegrees with statistics (stats may be NULL):
+ * device_ms (= init_ms) of the whole pass, edges_traversed (CSR entries a
+ * plain single-source h-bounded BFS would scan, summed over all sources: the
+ * numerator of the pass's traversed-edges rate), level_bytes (algorithmic
+ * bytes of its BFS levels), source_batches, kernel_launches, and, while
+ * profiling is on, level_launches / level_ms of the level kernels.
+ */
+khcore_status khcore_hdegrees_ex(khcore_ctx *ctx, int32_t h, int32_t *deg_out, khcore_stats *stats);
+
+/*
  * khcore_hdegrees_of — d_v^h(G) for the listed vertices only (a subset of
  * the sources of khcore_hdegrees; same BFS, fewer batches).
  *   count    number of listed vertices, 0 <= count <= n

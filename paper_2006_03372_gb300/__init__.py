@@ -31,7 +31,7 @@ __all__ = [
     "khcore_set_push_alpha", "khcore_set_round_loop", "khcore_set_wait_limit", "khcore_set_round_words", "khcore_set_lazy", "khcore_set_graph_blocks",
     "khcore_status_string", "Stats",
     "KHCore", "library_path", "load_library", "khcore_batch_create", "khcore_batch_decompose", "pack_graphs",
-    "khcore_hdegrees_of", "khcore_hdegrees_static", "Server", "request_bytes",
+    "khcore_hdegrees_of", "khcore_hdegrees_ex", "khcore_hdegrees_static", "Server", "request_bytes",
 ]
 
 STATUS = {0: "KHCORE_OK", 1: "KHCORE_EINVAL", 2: "KHCORE_ENOMEM", 3: "KHCORE_ECUDA",
@@ -118,6 +118,8 @@ def load_library(build_if_missing: bool = False):
         lib.khcore_num_vertices.restype = i32
         lib.khcore_num_entries.argtypes = [P]
         lib.khcore_num_entries.restype = i64
+        lib.khcore_hdegrees_ex.argtypes = [P, i32, P, P]
+        lib.khcore_hdegrees_ex.restype = ctypes.c_int
         lib.khcore_hdegrees_of.argtypes = [P, i32, i32, P, P]
         lib.khcore_hdegrees_of.restype = ctypes.c_int
         lib.khcore_hdegrees_static.argtypes = [i32, i64, P, P, i32, i32, P, P, P]
@@ -273,6 +275,16 @@ def khcore_hdegrees(ctx, h: int, deg_out=None):
     p, _ = _ptr(out)
     _check(lib, ctx, lib.khcore_hdegrees(ctx, int(h), p))
     return out
+
+
+def khcore_hdegrees_ex(ctx, h: int, deg_out=None):
+    """(deg, stats) of the all-vertex h-degree pass."""
+    lib = load_library()
+    out = _out(ctx, deg_out)
+    p, _ = _ptr(out)
+    stats = Stats()
+    _check(lib, ctx, lib.khcore_hdegrees_ex(ctx, int(h), p, ctypes.byref(stats)))
+    return out, stats.as_dict()
 
 
 def khcore_hdegrees_of(ctx, h: int, verts, deg_out=None):

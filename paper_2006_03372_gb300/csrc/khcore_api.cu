@@ -1114,25 +1114,62 @@ khcore_status khcore_set_profiling(khcore_ctx *c, int32_t on)
     return KHCORE_OK;
 }
 
-khcore_status khcore_hdegrees(khcore_ctx *c, int32_t h, int32_t *deg_out)
+khcore_status khcore_hdegrees_ex(khcore_ctx *c, int32_t h, int32_t *deg_out, khcore_stats *stats)
 {
     khcore_status s = check_ctx(c);
     if (s != KHCORE_OK) return s;
     if (h < 1) return fail(c, KHCORE_EINVAL, "h must be >= 1 (got %d)", h);
     if (!deg_out && c->n) return fail(c, KHCORE_EINVAL, "deg_out is NULL");
-    if (c->n == 0) return KHCORE_OK;
+    khcore_stats stt;
+    std::memset(&stt, 0, sizeof stt);
+    if (c->n == 0) {
+        if (stats) *stats = stt;
+        return KHCORE_OK;
+    }
     const int W = c->W_req ? c->W_req : auto_words(c->n);
     if ((s = ensure_bfs(c, W)) != KHCORE_OK) return s;
     if ((s = clear_if_dirty(c)) != KHCORE_OK) return s;
     int32_t hmax = 1;
     for (int32_t g = 0; g < c->G; g++) hmax = std::max(hmax, effective_h(c->v_off[g + 1] - c->v_off[g], h));
+    stt.h = hmax;
+    stt.words_per_vertex = W;
+    c->level_ms = 0.0;
+    c->level_launches = 0;
+    c->timer.used = 0;
+    CU(cudaMemsetAsync(c->edges, 0, sizeof(unsigned long long), c->stream));
+    CU(cudaMemsetAsync(c->alg, 0, sizeof(unsigned long long), c->stream));
+    CU(cudaEventRecord(c->ev0, c->stream));
     CU(launch_alive_init(c->alive, c->n, c->stream));
     CU(launch_iota(c->src, c->n, c->stream));
+    stt.kernel_launches += 2;
     // graphs are disjoint: one BFS over the union gives every graph's h-degrees
-    if ((s = hdeg_sources(c, W, hmax, c->src, c->n, c->n, c->m, nullptr)) != KHCORE_OK) return s;
+    if ((s = hdeg_sources(c, W, hmax, c->src, c->n, c->n, c->m, &stt)) != KHCORE_OK) return s;
+    CU(cudaEventRecord(c->ev1, c->stream));
     if ((s = write_out(c, deg_out, c->deg)) != KHCORE_OK) return s;
+    unsigned long long edges = 0, alg = 0;
+    CU(cudaMemcpyAsync(&edges, c->edges, sizeof edges, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(&alg, c->alg, sizeof alg, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
+    if (stats) {
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+        if ((s = flush_timer(c)) != KHCORE_OK) return s;
+        stt.device_ms = ms;
+        stt.init_ms = ms;
+        stt.edges_traversed = (int64_t)edges;
+        stt.level_bytes = (double)alg;
+        stt.level_ms = c->level_ms;
+        stt.level_launches = c->level_launches;
+        *stats = stt;
+    } else if ((s = flush_timer(c)) != KHCORE_OK) {
+        return s;
+    }
     return KHCORE_OK;
+}
+
+khcore_status khcore_hdegrees(khcore_ctx *c, int32_t h, int32_t *deg_out)
+{
+    return khcore_hdegrees_ex(c, h, deg_out, nullptr);
 }
 
 khcore_status khcore_hdegrees_of(khcore_ctx *c, int32_t h, int32_t count, const int32_t *verts, int32_t *deg_out)

@@ -304,3 +304,19 @@ def test_graph_blocks_single_graphs(kh, h):
             c2, r2, st2 = ctx.decompose_ex(h)
         assert (c == want).all(), (g.name, h)
         assert (r == r2).all() and st["rounds"] == st2["rounds"], (g.name, h)
+
+
+def test_hdegrees_ex_statistics(kh):
+    """khcore_hdegrees_ex returns the same h-degrees as the oracle and counts
+    the traversed edges of a plain single-source BFS from every vertex (at
+    h = 1: the sum of the degrees; at h = 2: sum of deg(v) + sum over
+    neighbours of deg(u), i.e. sum deg + sum deg^2)."""
+    g = gg.chung_lu(3000, 8.0, 2.5, 200.0, 88)
+    deg = np.diff(g.row_ptr).astype(np.int64)
+    with kh.KHCore.from_graph(g) as ctx:
+        d1, st1 = kh.khcore_hdegrees_ex(ctx.ctx, 1)
+        d2, st2 = kh.khcore_hdegrees_ex(ctx.ctx, 2)
+    assert (d1 == oracle.hdegrees(g, 1)).all() and (d2 == oracle.hdegrees(g, 2)).all()
+    assert st1["edges_traversed"] == int(deg.sum())
+    assert st2["edges_traversed"] == int(deg.sum() + (deg * deg).sum())
+    assert st2["device_ms"] > 0 and st2["source_batches"] >= 1 and st2["level_bytes"] > 0
