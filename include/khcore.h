@@ -299,15 +299,17 @@ khcore_status khcore_set_lazy(khcore_ctx *ctx, int32_t on);
 khcore_status khcore_set_round_loop(khcore_ctx *ctx, int32_t mode);
 
 /*
- * khcore_set_graph_blocks — for contexts of many small graphs: one thread
- * block decomposes each whole graph (initial h-degrees and every round), the
- * blocks taking graphs largest first, with no grid-wide barrier and no host
- * round trip; the grid stays busy with other graphs while one graph runs its
- * rounds. mode 0 (default): used when the context holds at least 64 graphs
- * and none has more than 8,192 vertices; 1: always; -1: never. Results
- * are identical either way (the per-block path recomputes the inner affected
- * vertices eagerly; khcore_set_lazy and khcore_set_round_loop do not apply
- * to it). EINVAL for other modes.
+ * khcore_set_graph_blocks — how a context of several graphs is decomposed.
+ * mode 0 (default): the graphs of at most 4,096 vertices are decomposed whole
+ * by one thread block each (initial h-degrees and every round), in one launch
+ * with no grid-wide barrier and no host round trip, the blocks taking graphs
+ * largest first; then every larger graph runs alone on the grid-wide path
+ * (its own persistent launch over a copy of its CSR). mode 1: every graph on
+ * one block. mode -1: all graphs' rounds in lock-step on the grid-wide path
+ * (one launch over the union). Contexts of one graph use the grid-wide path
+ * unless mode is 1. Results are identical in every mode; the per-block path
+ * recomputes the inner affected vertices eagerly (khcore_set_lazy and
+ * khcore_set_round_loop do not apply to it). EINVAL for other modes.
  */
 khcore_status khcore_set_graph_blocks(khcore_ctx *ctx, int32_t mode);
 

@@ -345,8 +345,12 @@ khcore_status hdeg_sources(khcore_ctx *c, int W, int32_t h, const int32_t *src, 
             khcore_status s = flush_timer(c);
             if (s != KHCORE_OK) return s;
         }
-        CU(run_bfs_batch(W, g, c->alive, b, src + off, cur, h, c->deg, tune, grid, c->stream,
-                         stt ? &stt->kernel_launches : nullptr, c->profiling ? &c->timer : nullptr));
+        // a batch of at most 64 sources runs on one-word rows (a quarter of
+        // the row traffic of W = 4; the row arrays are all zero between
+        // batches in either layout)
+        const int Wb = (W > 1 && cur <= 64) ? 1 : W;
+        CU(run_bfs_batch(Wb, g, c->alive, b, src + off, cur, h, c->deg, tune, Wb == W ? grid : bfs_grid(c, Wb),
+                         c->stream, stt ? &stt->kernel_launches : nullptr, c->profiling ? &c->timer : nullptr));
         if (stt) {
             stt->source_batches++;
         }
@@ -534,6 +538,49 @@ khcore_status finish_decompose(khcore_ctx *c, int32_t G, int32_t *core_out, int3
     return KHCORE_OK;
 }
 
+khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t *core_out, int32_t *round_out,
+                        khcore_stats *stats);
+
+// Graph gi of a batch context decomposed alone on the grid-wide path: a
+// context of its own over a copy of its CSR (local ids), the same stream and
+// settings; core indices and rounds go straight into c->core / c->rnd.
+khcore_status decompose_alone(khcore_ctx *c, int32_t gi, int32_t h, khcore_stats *sst)
+{
+    const int64_t v0 = c->v_off[gi];
+    const int32_t ng = (int32_t)(c->v_off[gi + 1] - v0);
+    std::vector<int32_t> rp((size_t)ng + 1);
+    CU(cudaMemcpyAsync(rp.data(), c->row_ptr + v0, sizeof(int32_t) * rp.size(), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    const int32_t e0 = rp[0];
+    for (auto &x : rp) x -= e0;
+    std::vector<int32_t> col((size_t)rp[ng]);
+    if (!col.empty()) {
+        CU(cudaMemcpyAsync(col.data(), c->col + e0, sizeof(int32_t) * col.size(), cudaMemcpyDeviceToHost,
+                           c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+    }
+    for (auto &x : col) x -= (int32_t)v0;
+    khcore_ctx *sub = nullptr;
+    khcore_status s = khcore_create(ng, rp.data(), col.empty() ? nullptr : col.data(), KHCORE_FLAG_TRUST_INPUT,
+                                    c->stream, &sub);
+    if (s != KHCORE_OK) return fail(c, s, "graph %d alone: %s", gi, khcore_last_error(nullptr));
+    sub->W_req = c->W_req;
+    sub->Wr_req = c->Wr_req;
+    sub->push_alpha = c->push_alpha;
+    sub->lazy = c->lazy;
+    sub->round_loop = c->round_loop;
+    sub->wait_limit_ns = c->wait_limit_ns;
+    s = decompose(sub, std::vector<int32_t>{h}, c->core + v0, c->rnd + v0, sst);
+    if (s != KHCORE_OK) {
+        const std::string msg = sub->err;
+        if (s == KHCORE_ETIMEOUT) c->dirty = true;
+        khcore_destroy(sub);
+        return fail(c, s, "graph %d alone: %s", gi, msg.c_str());
+    }
+    khcore_destroy(sub);
+    return KHCORE_OK;
+}
+
 // The decomposition driver. h_in[g] is the hop bound of graph g (g < c->G).
 khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t *core_out, int32_t *round_out,
                         khcore_stats *stats)
@@ -635,63 +682,91 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
     // the host vectors above must outlive the async copies
     CU(cudaStreamSynchronize(c->stream));
 
-    // Many small graphs: one thread block decomposes each whole graph, with no
-    // grid-wide barrier (khcore_block.cu).
-    int32_t nmax = 0;
-    for (int32_t gi = 0; gi < G; gi++) nmax = std::max<int32_t>(nmax, (int32_t)(c->v_off[gi + 1] - c->v_off[gi]));
-    const bool blocks = c->graph_blocks > 0 || (c->graph_blocks == 0 && G >= kBlockGraphsMinCount &&
-                                                nmax <= kBlockGraphsMaxN);
-    if (blocks) {
-        std::vector<int32_t> order(G);
-        for (int32_t gi = 0; gi < G; gi++) order[gi] = gi;
-        std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+    // Batches (mode 0 with G >= 2, or mode 1): graphs of at most
+    // kBlockGraphsMaxN vertices (mode 1: all graphs) are decomposed whole by
+    // one thread block each, in one launch with no grid-wide barrier
+    // (khcore_block.cu); each larger graph then runs alone on the grid-wide
+    // path, in a context of its own over a copy of its CSR.
+    const bool all_blocks = c->graph_blocks > 0;
+    if (all_blocks || (c->graph_blocks == 0 && G >= 2)) {
+        std::vector<int32_t> small, large;
+        for (int32_t gi = 0; gi < G; gi++)
+            (all_blocks || c->v_off[gi + 1] - c->v_off[gi] <= kBlockGraphsMaxN ? small : large).push_back(gi);
+        std::stable_sort(small.begin(), small.end(), [&](int32_t x, int32_t y) {
             return c->v_off[x + 1] - c->v_off[x] > c->v_off[y + 1] - c->v_off[y];
         });
-        CU(cudaMemcpyAsync(c->order_d, order.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, c->stream));
-        CU(cudaMemsetAsync(c->bnext, 0, sizeof(int32_t), c->stream));
-        CU(cudaMemsetAsync(c->bstats, 0, sizeof(BlockStats), c->stream));
         CU(cudaEventRecord(c->ev_init, c->stream));
-        BlockLaunch L;
-        L.rp = c->row_ptr;
-        L.col = c->col;
-        L.voff = c->voff_d;
-        L.hg = c->hg;
-        L.order = c->order_d;
-        L.count = G;
-        L.next = c->bnext;
-        L.alive = c->alive;
-        L.deg = c->deg;
-        L.core = c->core;
-        L.rnd = c->rnd;
-        L.kg = c->kg;
-        L.V = c->V;
-        L.F0 = c->F[0];
-        L.F1 = c->F[1];
-        L.live0 = c->src;
-        L.live1 = c->comb;
-        L.qa = c->Q[0];
-        L.qb = c->Q[1];
-        L.tl = c->T;
-        L.al = c->Q[2];
-        L.dl = c->dcls;
-        L.sl = c->cand;
-        L.mark = c->slack;  // zero here (cleared above) and left zero
-        L.dcount = c->dcount;
-        L.edges = c->edges;
-        L.bs = c->bstats;
-        const int bgrid = std::min(G, c->sm_count * max_blocks_per_sm_block_decompose());
-        CU(launch_decompose_blocks(L, bgrid, c->stream));
-        BlockStats bsh;
-        CU(cudaMemcpyAsync(&bsh, c->bstats, sizeof bsh, cudaMemcpyDeviceToHost, c->stream));
-        CU(cudaStreamSynchronize(c->stream));
-        stt.kernel_launches += 1;
         stt.words_per_vertex = 1;
-        stt.rounds = (int32_t)bsh.rounds;
-        stt.source_batches += bsh.batches;
-        stt.affected_total += bsh.affected;
-        stt.recomputed_total += bsh.recomputed;
+        if (!small.empty()) {
+            const int32_t ns = (int32_t)small.size();
+            CU(cudaMemcpyAsync(c->order_d, small.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, c->stream));
+            CU(cudaMemsetAsync(c->bnext, 0, sizeof(int32_t), c->stream));
+            CU(cudaMemsetAsync(c->bstats, 0, sizeof(BlockStats), c->stream));
+            BlockLaunch L;
+            L.rp = c->row_ptr;
+            L.col = c->col;
+            L.voff = c->voff_d;
+            L.hg = c->hg;
+            L.order = c->order_d;
+            L.count = ns;
+            L.next = c->bnext;
+            L.alive = c->alive;
+            L.deg = c->deg;
+            L.core = c->core;
+            L.rnd = c->rnd;
+            L.kg = c->kg;
+            L.V = c->V;
+            L.F0 = c->F[0];
+            L.F1 = c->F[1];
+            L.live0 = c->src;
+            L.live1 = c->comb;
+            L.qa = c->Q[0];
+            L.qb = c->Q[1];
+            L.tl = c->T;
+            L.al = c->Q[2];
+            L.dl = c->dcls;
+            L.sl = c->cand;
+            L.mark = c->slack;  // zero here (cleared above) and left zero
+            L.dcount = c->dcount;
+            L.edges = c->edges;
+            L.bs = c->bstats;
+            const int bgrid = std::min(ns, c->sm_count * max_blocks_per_sm_block_decompose());
+            CU(launch_decompose_blocks(L, bgrid, c->stream));
+            BlockStats bsh;
+            CU(cudaMemcpyAsync(&bsh, c->bstats, sizeof bsh, cudaMemcpyDeviceToHost, c->stream));
+            CU(cudaStreamSynchronize(c->stream));
+            stt.kernel_launches += 1;
+            stt.rounds = (int32_t)bsh.rounds;
+            stt.source_batches += bsh.batches;
+            stt.affected_total += bsh.affected;
+            stt.recomputed_total += bsh.recomputed;
+        }
         stt.deleted_total += c->n;
-        return finish_decompose(c, G, core_out, round_out, stats, stt, true);
+        khcore_stats sub_sum;
+        std::memset(&sub_sum, 0, sizeof sub_sum);
+        std::vector<int32_t> kg_large;
+        for (int32_t gi : large) {
+            khcore_stats sst;
+            if ((s = decompose_alone(c, gi, h_in[gi], &sst)) != KHCORE_OK) return s;
+            kg_large.push_back(sst.k_max);
+            stt.rounds = std::max(stt.rounds, sst.rounds);
+            stt.source_batches += sst.source_batches;
+            stt.kernel_launches += sst.kernel_launches;
+            stt.affected_total += sst.affected_total;
+            stt.recomputed_total += sst.recomputed_total;
+            sub_sum.edges_traversed += sst.edges_traversed;
+            sub_sum.level_bytes += sst.level_bytes;
+            sub_sum.round_bytes += sst.round_bytes;
+        }
+        for (size_t i = 0; i < large.size(); i++)
+            CU(cudaMemcpyAsync(c->kg + large[i], &kg_large[i], sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+        if ((s = finish_decompose(c, G, core_out, round_out, stats, stt, true)) != KHCORE_OK) return s;
+        if (stats) {
+            stats->edges_traversed += sub_sum.edges_traversed;
+            stats->level_bytes += sub_sum.level_bytes;
+            stats->round_bytes += sub_sum.round_bytes;
+        }
+        return KHCORE_OK;
     }
 
     // initial h-degrees, class by class

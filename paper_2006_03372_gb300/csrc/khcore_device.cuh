@@ -810,26 +810,35 @@ __device__ __forceinline__ void dev_min_over_list(const int32_t *list, int32_t c
 
 // k_g <- max(k_g, min alive deg of g) (Algorithm 1 moves a vertex to
 // B[max{k, d}], so the level never falls); reset the per-round counters.
-__device__ __forceinline__ void dev_set_level(PeelView p, PeelState *st)
+__device__ __forceinline__ void set_level_part(PeelView p, PeelState *st, int32_t i0, int32_t step, bool leader)
 {
-    for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < p.G; g += gridDim.x * blockDim.x) {
+    for (int32_t g = i0; g < p.G; g += step) {
         const int32_t m = p.ming[g];
         if (m != INT_MAX && m > p.kg[g]) p.kg[g] = m;
         p.ming[g] = INT_MAX;
         if (p.mind) p.mind[g] = INT_MAX;
         if (p.minub) p.minub[g] = INT_MAX;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (leader) {
         st->nD = 0;
         st->nA = 0;
         st->aq[0] = st->aq[1] = st->aq[2] = 0;
     }
-    for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < p.ncls; c += gridDim.x * blockDim.x) {
+    for (int32_t c = i0; c < p.ncls; c += step) {
         p.nAc[c] = 0;
         p.nDc[c] = 0;
         if (p.ncand) p.ncand[c] = 0;
     }
 }
+
+__device__ __forceinline__ void dev_set_level(PeelView p, PeelState *st)
+{
+    set_level_part(p, st, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x,
+                   blockIdx.x == 0 && threadIdx.x == 0);
+}
+
+// The same on one thread (few graphs: run inside a grid barrier's serial step).
+__device__ __forceinline__ void dev_set_level_serial(PeelView p, PeelState *st) { set_level_part(p, st, 0, 1, true); }
 
 // D = {alive v : deg[v] <= k_g(v)}: core[v] = k, rnd[v] = round, clear the
 // alive bit, append v to dlist (st->aq[0]) and to its class region of dcls.

@@ -248,10 +248,9 @@ struct PersistLaunch {
 // range of the graph it works on. V, F0, F1 (one 64-bit row per vertex),
 // mark and dcount are zero on entry and on exit; the list arrays (n entries
 // each) are scratch.
-// Automatic choice of the per-block path: at least this many graphs, none
-// larger than this many vertices.
-constexpr int32_t kBlockGraphsMinCount = 64;
-constexpr int32_t kBlockGraphsMaxN = 1 << 13;
+// Batches: graphs of at most this many vertices go to the per-block path
+// (above it one block per graph is slower than the grid-wide path alone).
+constexpr int32_t kBlockGraphsMaxN = 1 << 12;
 struct BlockStats {
     long long rounds;      // largest per-graph round count
     long long batches;     // BFS batches of 64 sources

@@ -149,18 +149,23 @@ __device__ bool bfs_batch(const PersistArgs &a, const int32_t *src, int32_t ns, 
         if (!grid_sync(a.gs, a.timeout_ns, [&] { a.ps->level_steps++; })) return false;
         tune.m_alive = *((volatile unsigned long long *)&a.st->m_alive);
         tune.n_alive = *((volatile int32_t *)&a.st->alive);
-        if (lvl == h - 1)
+        if (lvl == h - 1) {
+            // the last level reads the visited rows and the touched list
+            // without changing them, so the weights of the sources within
+            // h-1 are taken in the same phase
+            if (b.wsum && h >= 2) dev_weight_pass<W>(b, src, a.g.row_ptr, a.alive, true);
             dev_level<W, true>(a.g, a.alive, b, lvl, tune);
-        else
+        } else {
             dev_level<W, false>(a.g, a.alive, b, lvl, tune);
+        }
         if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return false;
         if (lvl == h - 1)
             dev_post<W, true>(a.g, b, lvl, tune);
         else
             dev_post<W, false>(a.g, b, lvl, tune);
-        if (b.wsum && (lvl == h - 2 || lvl == h - 3)) {
+        if (b.wsum && lvl == h - 3) {
             if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return false;
-            dev_weight_pass<W>(b, src, a.g.row_ptr, a.alive, lvl == h - 2);
+            dev_weight_pass<W>(b, src, a.g.row_ptr, a.alive, false);
         }
     }
     if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return false;
@@ -176,11 +181,21 @@ __device__ bool bfs_sources(const PersistArgs &a, const int32_t *src, int32_t ns
     constexpr int32_t S = 64 * W;
     for (int32_t off = 0; off < ns; off += S) {
         const int32_t cur = ns - off < S ? ns - off : S;
-        if (!bfs_batch<W>(a, src + off, cur, h, rowcnt, row_first > off ? row_first - off : 0, weights)) return false;
+        const int32_t rf = row_first > off ? row_first - off : 0;
+        // a batch of at most 64 sources runs on one-word rows: a quarter of
+        // the row traffic of W = 4 for the same result (the row arrays are
+        // all zero between batches in either layout)
+        const bool ok = (W > 1 && cur <= 64) ? bfs_batch<1>(a, src + off, cur, h, rowcnt, rf, weights)
+                                             : bfs_batch<W>(a, src + off, cur, h, rowcnt, rf, weights);
+        if (!ok) return false;
         if (blockIdx.x == 0 && threadIdx.x == 0) a.ps->source_batches++;
     }
     return true;
 }
+
+// Contexts with at most this many graphs update the levels on one thread
+// inside a barrier (one barrier less per round).
+constexpr int32_t kSerialLevelMaxGraphs = 64;
 
 template <int W>
 __global__ void __launch_bounds__(kBlock, (W <= 4 ? 2 : 1)) k_decompose(PersistArgs a)
@@ -197,9 +212,14 @@ __global__ void __launch_bounds__(kBlock, (W <= 4 ? 2 : 1)) k_decompose(PersistA
     };
     // the initial h-degrees are in deg already (computed by the per-phase
     // kernels at the widest W); the rounds follow
-    for (;;) {
-        // level of every graph: k_g <- max(k_g, min alive h-degree)
-        if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
+    const bool serial_level = a.p.G <= kSerialLevelMaxGraphs;
+    for (bool first = true;; first = false) {
+        // level of every graph: k_g <- max(k_g, min alive h-degree); the
+        // barrier closing the previous round advances the round counter
+        if (!grid_sync(a.gs, a.timeout_ns, [&] {
+                if (!first) a.st->round++;
+            }))
+            return;
         mark(4);
         dev_min_alive_deg(a.g.n, a.alive, a.deg, a.p);
         if (a.p.slack) {
@@ -220,12 +240,17 @@ __global__ void __launch_bounds__(kBlock, (W <= 4 ? 2 : 1)) k_decompose(PersistA
                 if (blockIdx.x == 0 && threadIdx.x == 0) a.ps->recomputed_total += nc;
             }
         }
-        if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
+        // few graphs: the level step runs inside the barrier
+        if (!grid_sync(a.gs, a.timeout_ns, [&] {
+                if (serial_level) dev_set_level_serial(a.p, a.st);
+            }))
+            return;
         mark(a.p.slack ? 1 : 0);
-        dev_set_level(a.p, a.st);
+        if (!serial_level) {
+            dev_set_level(a.p, a.st);
+            if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
+        }
         // peel set D
-        if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
-        mark(0);
         dev_peel_compact(a.g.n, a.g.row_ptr, a.alive, a.deg, a.p, a.st, a.core, a.rnd, a.vis, a.aq[0], a.dcls);
         // affected set A: BFS from D through survivors; snapshot the per-class
         // counts before the level that reaches distance h of each class
@@ -285,7 +310,6 @@ __global__ void __launch_bounds__(kBlock, (W <= 4 ? 2 : 1)) k_decompose(PersistA
                 dev_apply_dcount(Ac, ni, na, single ? nullptr : a.dcount, a.deg);
             }
         }
-        if (!grid_sync(a.gs, a.timeout_ns, [&] { a.st->round++; })) return;
     }
 }
 

@@ -174,6 +174,7 @@ def test_batch_matches_solo_oracle(kh):
     v_off, e_off, rp, col = kh.pack_graphs(graphs)
     ctx = kh.khcore_batch_create(v_off, e_off, rp, col)
     try:
+        kh.khcore_set_graph_blocks(ctx, -1)  # the lock-step union path
         for w, loop in [(1, 0), (4, 1), (16, 0)]:
             kh.khcore_set_words(ctx, w)
             kh.khcore_set_round_loop(ctx, loop)
@@ -271,7 +272,7 @@ def _batch_graphs(seed, count, nmax):
 def test_graph_blocks_batch_matches_solo_oracle_and_grid_path(kh):
     """A batch of 81 small graphs takes the one-block-per-graph path by
     default: each graph's core indices equal the oracle's on that graph alone,
-    and cores and rounds equal the grid-wide path's."""
+    and cores and rounds equal the lock-step union path's."""
     graphs, hs = _batch_graphs(81, 80, 150)
     v_off, e_off, rp, col = kh.pack_graphs(graphs)
     ctx = kh.khcore_batch_create(v_off, e_off, rp, col)
@@ -320,3 +321,29 @@ def test_hdegrees_ex_statistics(kh):
     assert st1["edges_traversed"] == int(deg.sum())
     assert st2["edges_traversed"] == int(deg.sum() + (deg * deg).sum())
     assert st2["device_ms"] > 0 and st2["source_batches"] >= 1 and st2["level_bytes"] > 0
+
+
+def test_batch_mixed_small_and_large_graphs(kh):
+    """Default batch mode: small graphs on one block each, the larger ones
+    (above 4,096 vertices) alone on the grid-wide path; every graph equals the
+    oracle (a cycle: 2h) and the lock-step union path."""
+    small, _ = _batch_graphs(91, 12, 200)
+    big = [gg.chung_lu(5000, 6.0, 2.5, 80.0, 92), gg.cycle(4300)]
+    graphs = small[:6] + big[:1] + small[6:] + big[1:]
+    hs = np.array([2, 3, 1, 4, 2, 3, 2, 2, 3, 1, 2, 4, 3, 3, 3], dtype=np.int32)[:len(graphs)]
+    v_off, e_off, rp, col = kh.pack_graphs(graphs)
+    ctx = kh.khcore_batch_create(v_off, e_off, rp, col)
+    try:
+        core, rnd, st = kh.khcore_batch_decompose(ctx, hs)
+        kh.khcore_set_graph_blocks(ctx, -1)
+        core2, rnd2, st2 = kh.khcore_batch_decompose(ctx, hs)
+    finally:
+        kh.khcore_destroy(ctx)
+    assert (core == core2).all() and (rnd == rnd2).all()
+    for g, h, a, b in zip(graphs, hs, v_off[:-1], v_off[1:]):
+        if g is big[1]:
+            assert (core[a:b] == 2 * int(h)).all()
+        else:
+            assert (core[a:b] == oracle.peel(g, int(h))).all(), (g.name, h)
+        assert oracle.certificate(g, int(h), core[a:b], rnd[a:b])[0] == 0
+    assert st["k_max"] == st2["k_max"]
