@@ -130,6 +130,24 @@ def workload_name(args, g) -> str:
     return WORKLOAD if args.graph == "cl1m" else f"{args.graph}:{g.name}"
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# persistent round kernel on the headline workload, from one ncu capture of
+# `python bench.py --steps 1 --warmup 0 --no-cpu-baseline --e2e-steps 0`
+# (profiles/k_decompose_w4_cl1m_h2_dram.md), keyed by a digest of the kernel
+# sources it was taken on: reported only while the sources are unchanged.
+KERNEL_TRAFFIC = {}
+
+
+def kernel_source_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2006_03372_gb300", "csrc")
+    for name in ("khcore_persist.cuh", "khcore_device.cuh", "khcore_internal.cuh"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -367,7 +385,9 @@ def run_ours(args):
         "rounds": {str(h): st_last[h]["rounds"] for h in hs},
         "gteps": edges / (ms / 1e3) / 1e9,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak if achieved else None, "traffic": None,
+                     "frac": achieved / peak if achieved else None,
+                     "traffic": (KERNEL_TRAFFIC.get((args.graph, tuple(hs), kernel_source_digest()))
+                                 if rnd_ms >= lvl_ms else None),
                      "kernel": kname, "time_share": kshare, "peak_kind": peak_kind},
         "phase_ms": {"initial_pass": sum(s["init_ms"] for s in stats) / args.steps,
                      "rounds": rnd_ms / args.steps},
