@@ -92,11 +92,10 @@ void run_group(khcore_server *s, std::vector<Request *> &batch, cudaStream_t str
                                            KHCORE_FLAG_TRUST_INPUT, stream, &ctx);
     std::string msg;
     // small graphs: one block each (no grid barrier, so concurrent groups
-    // interleave freely); large graphs: each alone on the grid-wide path with
-    // host-driven rounds, whose small kernels interleave with other groups
-    // where a persistent kernel would hold every SM
+    // interleave freely); large graphs: each alone on the grid-wide path, its
+    // rounds in one persistent launch (host-driven rounds, one sync per
+    // round, left the larger requests far behind the offered load)
     if (st == KHCORE_OK) st = khcore_set_graph_blocks(ctx, blocks ? 1 : 0);
-    if (st == KHCORE_OK && !blocks) st = khcore_set_round_loop(ctx, 1);
     if (st == KHCORE_OK) {
         st = khcore_batch_decompose(ctx, h.data(), core.data(), nullptr, nullptr);
         if (st != KHCORE_OK) msg = khcore_last_error(ctx);
