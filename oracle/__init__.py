@@ -65,6 +65,10 @@ def _load():
         lib.orc_kcore_bz.restype = ctypes.c_int
         lib.orc_certificate.argtypes = [i32, P, P, i32, P, P, i64, P, P]
         lib.orc_certificate.restype = ctypes.c_int64
+        lib.orc_bitmap_update.argtypes = [i32, P, P, P, i32, i32, P, P, i64, P]
+        lib.orc_bitmap_update.restype = ctypes.c_int64
+        lib.orc_peel_bitmap.argtypes = [i32, P, P, i32, P, P]
+        lib.orc_peel_bitmap.restype = ctypes.c_int
         lib.orc_has_openmp.argtypes = []
         lib.orc_has_openmp.restype = ctypes.c_int
         _lib = lib
@@ -130,6 +134,41 @@ def peel(g, h: int, return_order: bool = False):
     rc = lib.orc_peel(g.n, _p(rp), _p(col), int(h), _p(core), _p(order))
     if rc != 0:
         raise RuntimeError(f"oracle peel failed ({rc})")
+    if return_order:
+        return core[: g.n], order[: g.n]
+    return core[: g.n]
+
+
+def bitmap_update(g, h: int, v: int, deg, alive=None, trace_cap: int = 0):
+    """The paper's update after deleting v from G[alive] (Sec. IV-A/IV-B,
+    Algorithms 3 and 4). deg: current h-degrees (copied). Returns (new_deg,
+    labels, trace): labels[i] = vertex of u_i (distance from v, then id);
+    trace[t][i] = first bitmap word of u_i after the initialisation (t = 0)
+    and after hop t, when the ball has at most trace_cap members."""
+    lib = _load()
+    rp, col = _csr(g)
+    d = np.ascontiguousarray(deg, dtype=np.int32).copy()
+    a = _alive(alive, g.n)
+    cap = max(int(trace_cap), 0)
+    tr = np.zeros(max((h + 1) * cap, 1), dtype=np.uint64)
+    lab = np.zeros(max(cap, 1), dtype=np.int32)
+    nr = lib.orc_bitmap_update(g.n, _p(rp), _p(col), _p(a), int(h), int(v), _p(d), _p(tr) if cap else None,
+                               cap, _p(lab) if cap else None)
+    if nr < 0:
+        raise RuntimeError("oracle bitmap update failed")
+    if cap and nr <= cap:
+        return d, lab[:nr].copy(), tr[: (h + 1) * nr].reshape(h + 1, nr).copy()
+    return d, None, None
+
+
+def peel_bitmap(g, h: int, return_order: bool = False):
+    """The paper's decomposition with the bitmap update (Algorithm 2)."""
+    lib = _load()
+    rp, col = _csr(g)
+    core = np.zeros(max(g.n, 1), dtype=np.int32)
+    order = np.zeros(max(g.n, 1), dtype=np.int32)
+    if lib.orc_peel_bitmap(g.n, _p(rp), _p(col), int(h), _p(core), _p(order)) != 0:
+        raise RuntimeError("oracle bitmap peel failed")
     if return_order:
         return core[: g.n], order[: g.n]
     return core[: g.n]

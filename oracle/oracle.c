@@ -21,6 +21,12 @@
  *                     contain v. Exponential; tiny graphs only.
  *   orc_kcore_bz      classic linear-time k-core by bin sort (Batagelj and
  *                     Zaversnik, cited in Sec. II), the h = 1 special case.
+ *   orc_bitmap_update the paper's exact h-degree update after one deletion
+ *                     (Sec. IV-A, Algorithm 3, with the bitmaps of Sec. IV-B,
+ *                     Algorithm 4): a reachability DP on the subgraph induced
+ *                     by N_v^h instead of a BFS per member.
+ *   orc_peel_bitmap   the paper's decomposition driving that update
+ *                     (Sec. IV-A, Algorithm 2).
  *   orc_certificate   checks a claimed core index c and peel round r against
  *                     two inequalities that together imply c is exact (the
  *                     argument is written above the function).
@@ -33,7 +39,10 @@
  *
  * Pins: tests/test_oracle_pins.py checks every routine against brute force,
  * closed forms, SciPy's all-pairs shortest paths, networkx.core_number at
- * h = 1, the paper's worked example (Example 1, Example 2) and invariants.
+ * h = 1, the paper's worked example (Example 1, Example 2, and Table 1's
+ * bitmaps for orc_bitmap_update) and invariants; orc_bitmap_update against a
+ * fresh BFS after every single deletion, orc_peel_bitmap against orc_peel and
+ * brute force.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -239,6 +248,180 @@ done:
     free(deg); free(head); free(next); free(prev); free(bucket);
     free(alive); free(dist); free(queue); free(ball);
     return removed;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The paper's h-degree update after deleting one vertex v (Sec. IV-A,       */
+/* Observation 2 and Theorem 1, Algorithm 3; with the bitmaps of Sec. IV-B,  */
+/* Algorithm 4). Works in G[alive] with v still alive; v itself is not       */
+/* removed here.                                                             */
+/*                                                                           */
+/*   R = N_v^h(G): the other vertices within h of v, labelled u_0, u_1, ...  */
+/*       by distance from v, then by vertex id (so N_v^{h-1} gets the first  */
+/*       d labels, as Table 1 shows: u_0..u_2 at distance 1, u_3, u_4 at 2). */
+/*   Reach(u_i) starts as {u_i} when dist(v, u_i) < h, else empty; then for  */
+/*   hop = 1..h every edge (u_i, u_j) of the subgraph induced by R ORs the   */
+/*   other end's set of the previous buffer into its own (two buffers,       */
+/*   alternating). Bit j of u_i's bitmap stands for u_j.                     */
+/*   New h-degree of u_i at distance s: the old one, minus 1 for v, minus 1  */
+/*   for every u_j with dist(v, u_j) <= h - s that Reach(u_i) misses.        */
+/*                                                                           */
+/* deg: in: h-degrees in G[alive]; out: those of R's members in G[alive]-v   */
+/* (other entries untouched). If trace != NULL and |R| <= trace_cap, the     */
+/* first 64-bit word of every member's bitmap after the initialisation and   */
+/* after each hop is stored at trace[t * |R| + i], t = 0..h, and labels[i] = */
+/* u_i's vertex id. Returns |R|, or -1 on ENOMEM.                            */
+/* ------------------------------------------------------------------------ */
+static int cmp_i32(const void *a, const void *b)
+{
+    const int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+int64_t orc_bitmap_update(int32_t n, const int32_t *row_ptr, const int32_t *col, const uint8_t *alive,
+                          int32_t h, int32_t v, int32_t *deg, uint64_t *trace, int64_t trace_cap,
+                          int32_t *labels)
+{
+    size_t N = (size_t)n;
+    int32_t *dist = malloc(sizeof(int32_t) * N);
+    int32_t *lab = malloc(sizeof(int32_t) * N);   /* vertex -> label, -1 outside R */
+    int32_t *queue = malloc(sizeof(int32_t) * N);
+    if (!dist || !lab || !queue) { free(dist); free(lab); free(queue); return -1; }
+    for (size_t i = 0; i < N; i++) { dist[i] = -1; lab[i] = -1; }
+
+    /* R by BFS from v inside G[alive], distances dis_G(v, .) */
+    int64_t head = 0, tail = 0;
+    queue[tail++] = v;
+    dist[v] = 0;
+    while (head < tail) {
+        int32_t x = queue[head++];
+        if (dist[x] == h) continue;
+        for (int32_t e = row_ptr[x]; e < row_ptr[x + 1]; e++) {
+            int32_t y = col[e];
+            if (alive && !alive[y]) continue;
+            if (dist[y] >= 0) continue;
+            dist[y] = dist[x] + 1;
+            queue[tail++] = y;
+        }
+    }
+    /* labels: queue[1..tail) is in nondecreasing distance; sort each level by id */
+    int32_t *R = queue + 1;
+    int64_t nr = tail - 1;
+    for (int64_t a = 0; a < nr;) {
+        int64_t b = a;
+        while (b < nr && dist[R[b]] == dist[R[a]]) b++;
+        qsort(R + a, (size_t)(b - a), sizeof(int32_t), cmp_i32);
+        a = b;
+    }
+    int64_t d = 0; /* |N_v^{h-1}|: the members that start with their own bit */
+    for (int64_t i = 0; i < nr; i++) {
+        lab[R[i]] = (int32_t)i;
+        if (dist[R[i]] < h) d++;
+    }
+    const int64_t W = d > 0 ? (d + 63) / 64 : 1;
+    uint64_t *reach[2];
+    reach[0] = calloc((size_t)(nr > 0 ? nr : 1) * (size_t)W, sizeof(uint64_t));
+    reach[1] = calloc((size_t)(nr > 0 ? nr : 1) * (size_t)W, sizeof(uint64_t));
+    if (!reach[0] || !reach[1]) {
+        free(reach[0]); free(reach[1]); free(dist); free(lab); free(queue);
+        return -1;
+    }
+    /* initialisation: Reach(u_i) = {u_i} for dist < h, in both buffers */
+    for (int64_t i = 0; i < d; i++) {
+        reach[0][i * W + i / 64] = 1ull << (i % 64);
+        reach[1][i * W + i / 64] = 1ull << (i % 64);
+    }
+    const int keep = trace && nr <= trace_cap;
+    if (keep) {
+        for (int64_t i = 0; i < nr; i++) { labels[i] = R[i]; trace[i] = reach[0][i * W]; }
+    }
+    /* the DP over the subgraph induced by R: each CSR entry (u_i -> u_j) is
+     * one direction of an edge of E(R) */
+    int p = 1, q = 0;
+    for (int32_t hop = 1; hop <= h; hop++) {
+        q = p;
+        p = 1 - p;
+        for (int64_t i = 0; i < nr; i++) {
+            int32_t x = R[i];
+            for (int32_t e = row_ptr[x]; e < row_ptr[x + 1]; e++) {
+                int32_t j = lab[col[e]];
+                if (j < 0) continue; /* v itself, dead or outside R */
+                for (int64_t b = 0; b < W; b++) reach[q][i * W + b] |= reach[p][(int64_t)j * W + b];
+            }
+        }
+        if (keep)
+            for (int64_t i = 0; i < nr; i++) trace[(int64_t)hop * nr + i] = reach[q][i * W];
+    }
+    /* the update */
+    for (int64_t i = 0; i < nr; i++) {
+        int32_t u = R[i];
+        int32_t s = dist[u];
+        int32_t nd = deg[u] - 1;
+        for (int64_t j = 0; j < nr; j++) {
+            if (dist[R[j]] > h - s) break; /* labels are in distance order */
+            if (!((reach[q][i * W + j / 64] >> (j % 64)) & 1ull)) nd--;
+        }
+        deg[u] = nd;
+    }
+    free(reach[0]); free(reach[1]); free(dist); free(lab); free(queue);
+    return nr;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The paper's decomposition with that update (Sec. IV-A, Algorithm 2):     */
+/* h-degrees of every vertex by BFS; then repeatedly k = the least h-degree */
+/* (never below the previous k), B = the alive vertices at <= k; while B is  */
+/* not empty, take its smallest vertex v, core(v) = k, update the h-degrees  */
+/* of N_v^h by orc_bitmap_update, add to B every member now at <= k, and     */
+/* delete v. Returns 0, or -1 on ENOMEM.                                     */
+/* ------------------------------------------------------------------------ */
+int orc_peel_bitmap(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t h,
+                    int32_t *core_out, int32_t *order_out)
+{
+    if (n == 0) return 0;
+    size_t N = (size_t)n;
+    int32_t *deg = malloc(sizeof(int32_t) * N);
+    uint8_t *alive = malloc(N);
+    uint8_t *inB = calloc(N, 1);
+    int32_t *dist = malloc(sizeof(int32_t) * N);
+    int32_t *queue = malloc(sizeof(int32_t) * N);
+    if (!deg || !alive || !inB || !dist || !queue) {
+        free(deg); free(alive); free(inB); free(dist); free(queue);
+        return -1;
+    }
+    for (size_t i = 0; i < N; i++) { alive[i] = 1; dist[i] = -1; }
+    for (int32_t v = 0; v < n; v++)
+        deg[v] = (int32_t)bfs_count(v, h, row_ptr, col, alive, dist, queue, NULL, NULL);
+    int32_t k = 0;
+    int64_t removed = 0;
+    while (removed < n) {
+        /* k <- min alive h-degree (not below the previous k) */
+        int32_t m = -1;
+        for (int32_t u = 0; u < n; u++)
+            if (alive[u] && (m < 0 || deg[u] < m)) m = deg[u];
+        if (m > k) k = m;
+        for (int32_t u = 0; u < n; u++)
+            if (alive[u] && deg[u] <= k) inB[u] = 1;
+        for (;;) {
+            int32_t v = -1;
+            for (int32_t u = 0; u < n; u++)
+                if (inB[u]) { v = u; break; }
+            if (v < 0) break;
+            inB[v] = 0;
+            core_out[v] = k;
+            if (order_out) order_out[removed] = v;
+            removed++;
+            if (orc_bitmap_update(n, row_ptr, col, alive, h, v, deg, NULL, 0, NULL) < 0) {
+                free(deg); free(alive); free(inB); free(dist); free(queue);
+                return -1;
+            }
+            alive[v] = 0;
+            for (int32_t u = 0; u < n; u++)
+                if (alive[u] && !inB[u] && deg[u] <= k) inB[u] = 1;
+        }
+    }
+    free(deg); free(alive); free(inB); free(dist); free(queue);
+    return 0;
 }
 
 /* ------------------------------------------------------------------------ */

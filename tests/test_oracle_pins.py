@@ -272,3 +272,67 @@ def test_peel_bounded_is_a_prefix_of_the_full_peel():
     assert r == 57 and (o2[:57] == order[:57]).all() and (c2[o2[:57]] == core[order[:57]]).all()
     r, c3, o3 = oracle.peel_bounded(g, 2, -1, deg_init=oracle.hdegrees(g, 2))
     assert r == g.n and (c3 == core).all()
+
+
+# ------------------------------------------- the paper's update (Alg. 2-4)
+
+def test_bitmap_update_reproduces_table1(fig1):
+    """Sec. IV-B, Table 1 and Example 3: labels, and every bitmap after the
+    initialisation and after each of the two DP iterations, for v5 in
+    G - {v1, v2, v3} at h = 2; then the update equals a fresh BFS."""
+    g, vals = fig1
+    alive = np.ones(g.n, np.uint8)
+    alive[[0, 1, 2]] = 0
+    deg = oracle.hdegrees(g, 2, alive)
+    new, labels, trace = oracle.bitmap_update(g, 2, 4, deg, alive, trace_cap=64)
+    assert list(labels + 1) == [int(x) for x in vals["table1_labels"]]
+    for t, key in enumerate(["table1_init", "table1_iter1", "table1_iter2"]):
+        assert list(trace[t]) == [int(x) for x in vals[key]], key
+    after = alive.copy()
+    after[4] = 0
+    fresh = oracle.hdegrees(g, 2, after)
+    assert (new[labels] == fresh[labels]).all()
+
+
+def test_bitmap_update_reproduces_example2(fig1):
+    """Sec. IV-A, Example 2: deleting v1 at h = 2 leaves d^2 = 3, 3, 7, 7 for
+    v2, v3, v4, v6."""
+    g, vals = fig1
+    deg = oracle.hdegrees(g, 2)
+    new, _, _ = oracle.bitmap_update(g, 2, 0, deg)
+    for item in vals["after_v1_hdeg2"]:
+        v, want = item.split(":")
+        assert new[int(v) - 1] == int(want)
+
+
+@pytest.mark.parametrize("h", [1, 2, 3, 4])
+def test_bitmap_update_equals_bfs_after_one_deletion(h):
+    """Observation 2 / Theorem 1: the DP on the ball's induced subgraph gives
+    exactly the h-degrees of G[alive] - v, on random alive subsets, including
+    balls of more than 64 members (several bitmap words)."""
+    rng = gg.Stream(500 + h, "bitmap")
+    graphs = small_graphs(600 + h, 8, (2, 60)) + [gg.chung_lu(400, 6.0, 2.3, 80.0, 31 + h), gg.star(150)]
+    for g in graphs:
+        for _ in range(4):
+            alive = (rng.uniform(g.n) < 0.85).astype(np.uint8)
+            cand = np.nonzero(alive)[0]
+            if len(cand) == 0:
+                continue
+            v = int(cand[rng.below(len(cand), 1)[0]])
+            deg = oracle.hdegrees(g, h, alive)
+            new, _, _ = oracle.bitmap_update(g, h, v, deg, alive)
+            after = alive.copy()
+            after[v] = 0
+            fresh = oracle.hdegrees(g, h, after)
+            keep = after.astype(bool)
+            assert (new[keep] == fresh[keep]).all(), (g.name, h, v)
+
+
+@pytest.mark.parametrize("h", [1, 2, 3, 4])
+def test_peel_bitmap_equals_algorithm1_and_bruteforce(h):
+    """Algorithm 2 with the bitmap update gives Algorithm 1's core indices,
+    and the definition's on tiny graphs."""
+    for g in small_graphs(700 + h, 10, (2, 80)):
+        assert (oracle.peel_bitmap(g, h) == oracle.peel(g, h)).all(), (g.name, h)
+    for g in small_graphs(800 + h, 6, (2, 11)):
+        assert (oracle.peel_bitmap(g, h) == oracle.bruteforce(g, h)).all(), (g.name, h)
