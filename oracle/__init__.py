@@ -69,6 +69,10 @@ def _load():
         lib.orc_bitmap_update.restype = ctypes.c_int64
         lib.orc_peel_bitmap.argtypes = [i32, P, P, i32, P, P]
         lib.orc_peel_bitmap.restype = ctypes.c_int
+        lib.orc_peel_sampled.argtypes = [i32, P, P, i32, P, P, P]
+        lib.orc_peel_sampled.restype = ctypes.c_int
+        lib.orc_sampled_estimate.argtypes = [i64, i64, i64]
+        lib.orc_sampled_estimate.restype = i32
         lib.orc_has_openmp.argtypes = []
         lib.orc_has_openmp.restype = ctypes.c_int
         _lib = lib
@@ -172,6 +176,25 @@ def peel_bitmap(g, h: int, return_order: bool = False):
     if return_order:
         return core[: g.n], order[: g.n]
     return core[: g.n]
+
+
+def peel_sampled(g, h: int, in_s):
+    """The sampling variant (Algorithms 5 and 6) with the sample given as a
+    0/1 mask: (core estimates, initial h-degree estimates)."""
+    lib = _load()
+    rp, col = _csr(g)
+    s = np.ascontiguousarray(in_s, dtype=np.uint8)
+    assert s.shape == (g.n,)
+    core = np.zeros(max(g.n, 1), dtype=np.int32)
+    est = np.zeros(max(g.n, 1), dtype=np.int32)
+    if lib.orc_peel_sampled(g.n, _p(rp), _p(col), int(h), _p(s), _p(core), _p(est)) != 0:
+        raise RuntimeError("oracle sampled peel failed")
+    return core[: g.n], est[: g.n]
+
+
+def sampled_estimate(sel: int, sel0: int, d0: int) -> int:
+    """select / rate with rate = sel0 / d0, rounded down, in integers."""
+    return int(_load().orc_sampled_estimate(int(sel), int(sel0), int(d0)))
 
 
 def peel_bounded(g, h: int, max_removed: int, deg_init=None):

@@ -27,6 +27,8 @@
  *                     by N_v^h instead of a BFS per member.
  *   orc_peel_bitmap   the paper's decomposition driving that update
  *                     (Sec. IV-A, Algorithm 2).
+ *   orc_peel_sampled  the paper's sampling variant (Sec. IV-C, Algorithms 5
+ *                     and 6) on a caller-drawn sample; approximate.
  *   orc_certificate   checks a claimed core index c and peel round r against
  *                     two inequalities that together imply c is exact (the
  *                     argument is written above the function).
@@ -42,7 +44,8 @@
  * h = 1, the paper's worked example (Example 1, Example 2, and Table 1's
  * bitmaps for orc_bitmap_update) and invariants; orc_bitmap_update against a
  * fresh BFS after every single deletion, orc_peel_bitmap against orc_peel and
- * brute force.
+ * brute force; orc_peel_sampled against the paper's estimator example and
+ * against Algorithm 1 when every vertex is sampled.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -423,6 +426,179 @@ int orc_peel_bitmap(int32_t n, const int32_t *row_ptr, const int32_t *col, int32
     free(deg); free(alive); free(inB); free(dist); free(queue);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* The paper's sampling variant (Sec. IV-C, Algorithms 5 and 6). The sample  */
+/* S is an input (in_s[v] != 0: v in S), drawn by the caller.                */
+/*                                                                           */
+/*   select[v] = |N_v^h(G) ∩ S| and rate[v] = select[v] / d_v^h(G) at the   */
+/*   start; the estimated h-degree is select[v] / rate[v], taken in exact    */
+/*   integer arithmetic and rounded down: floor(select * d0 / select0) (the  */
+/*   paper's example turns 8 / 0.45 into 17).                                */
+/*   Peeling as in Algorithm 2 on the estimates. Deleting v (Algorithm 6):   */
+/*   bitmaps only for the sampled members of N_v^{h-1}, the same DP on the   */
+/*   subgraph induced by N_v^h; every member u at distance s loses          */
+/*   cnt = [v in S] + |{sampled u_j, dist(v, u_j) <= h - s, not reached}|    */
+/*   from select[u] (<= as in Algorithm 4, so that S = V gives Algorithm 2   */
+/*   exactly).                                                               */
+/*   A vertex whose initial ball holds no sampled vertex (select0 = 0, d0 >  */
+/*   0) has no rate; its estimate drops by 1 for every deleted vertex within */
+/*   h of it.                                                                */
+/* core_out: the core estimates. Returns 0, or -1 on ENOMEM.                 */
+/* ------------------------------------------------------------------------ */
+static int32_t sampled_estimate(int64_t sel, int64_t sel0, int64_t d0, int32_t fallback)
+{
+    if (sel0 <= 0) return fallback;
+    if (sel <= 0) return 0;
+    return (int32_t)((sel * d0) / sel0);
+}
+
+static int64_t sampled_update(int32_t n, const int32_t *row_ptr, const int32_t *col, const uint8_t *alive,
+                              const uint8_t *in_s, int32_t h, int32_t v, int64_t *sel, const int64_t *sel0,
+                              const int32_t *d0, int32_t *est)
+{
+    size_t N = (size_t)n;
+    int32_t *dist = malloc(sizeof(int32_t) * N);
+    int32_t *lab = malloc(sizeof(int32_t) * N);
+    int32_t *queue = malloc(sizeof(int32_t) * N);
+    if (!dist || !lab || !queue) { free(dist); free(lab); free(queue); return -1; }
+    for (size_t i = 0; i < N; i++) { dist[i] = -1; lab[i] = -1; }
+    int64_t head = 0, tail = 0;
+    queue[tail++] = v;
+    dist[v] = 0;
+    while (head < tail) {
+        int32_t x = queue[head++];
+        if (dist[x] == h) continue;
+        for (int32_t e = row_ptr[x]; e < row_ptr[x + 1]; e++) {
+            int32_t y = col[e];
+            if (!alive[y] || dist[y] >= 0) continue;
+            dist[y] = dist[x] + 1;
+            queue[tail++] = y;
+        }
+    }
+    int32_t *R = queue + 1;
+    const int64_t nr = tail - 1;
+    for (int64_t a = 0; a < nr;) {
+        int64_t b = a;
+        while (b < nr && dist[R[b]] == dist[R[a]]) b++;
+        qsort(R + a, (size_t)(b - a), sizeof(int32_t), cmp_i32);
+        a = b;
+    }
+    /* bit index: the sampled members of N_v^{h-1}, in label order */
+    int32_t *bit = malloc(sizeof(int32_t) * (size_t)(nr > 0 ? nr : 1));
+    if (!bit) { free(dist); free(lab); free(queue); return -1; }
+    int64_t d = 0;
+    for (int64_t i = 0; i < nr; i++) {
+        lab[R[i]] = (int32_t)i;
+        bit[i] = (dist[R[i]] < h && in_s[R[i]]) ? (int32_t)d++ : -1;
+    }
+    const int64_t W = d > 0 ? (d + 63) / 64 : 1;
+    uint64_t *reach[2];
+    reach[0] = calloc((size_t)(nr > 0 ? nr : 1) * (size_t)W, sizeof(uint64_t));
+    reach[1] = calloc((size_t)(nr > 0 ? nr : 1) * (size_t)W, sizeof(uint64_t));
+    if (!reach[0] || !reach[1]) {
+        free(reach[0]); free(reach[1]); free(bit); free(dist); free(lab); free(queue);
+        return -1;
+    }
+    for (int64_t i = 0; i < nr; i++)
+        if (bit[i] >= 0) {
+            reach[0][i * W + bit[i] / 64] = 1ull << (bit[i] % 64);
+            reach[1][i * W + bit[i] / 64] = 1ull << (bit[i] % 64);
+        }
+    int p = 1, q = 0;
+    for (int32_t hop = 1; hop <= h; hop++) {
+        q = p;
+        p = 1 - p;
+        for (int64_t i = 0; i < nr; i++) {
+            int32_t x = R[i];
+            for (int32_t e = row_ptr[x]; e < row_ptr[x + 1]; e++) {
+                int32_t j = lab[col[e]];
+                if (j < 0) continue;
+                for (int64_t b = 0; b < W; b++) reach[q][i * W + b] |= reach[p][(int64_t)j * W + b];
+            }
+        }
+    }
+    for (int64_t i = 0; i < nr; i++) {
+        int32_t u = R[i];
+        int32_t s = dist[u];
+        int64_t cnt = in_s[v] ? 1 : 0;
+        for (int64_t j = 0; j < nr; j++) {
+            if (dist[R[j]] > h - s) break;
+            if (bit[j] < 0) continue; /* not sampled */
+            if (!((reach[q][i * W + bit[j] / 64] >> (bit[j] % 64)) & 1ull)) cnt++;
+        }
+        sel[u] -= cnt;
+        est[u] = sampled_estimate(sel[u], sel0[u], d0[u], est[u] - 1);
+    }
+    free(reach[0]); free(reach[1]); free(bit); free(dist); free(lab); free(queue);
+    return nr;
+}
+
+int orc_peel_sampled(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t h, const uint8_t *in_s,
+                     int32_t *core_out, int32_t *est_init_out)
+{
+    if (n == 0) return 0;
+    size_t N = (size_t)n;
+    int32_t *d0 = malloc(sizeof(int32_t) * N);
+    int32_t *est = malloc(sizeof(int32_t) * N);
+    int64_t *sel = malloc(sizeof(int64_t) * N);
+    int64_t *sel0 = malloc(sizeof(int64_t) * N);
+    uint8_t *alive = malloc(N);
+    uint8_t *inB = calloc(N, 1);
+    int32_t *dist = malloc(sizeof(int32_t) * N);
+    int32_t *queue = malloc(sizeof(int32_t) * N);
+    int32_t *ball = malloc(sizeof(int32_t) * N);
+    if (!d0 || !est || !sel || !sel0 || !alive || !inB || !dist || !queue || !ball) {
+        free(d0); free(est); free(sel); free(sel0); free(alive); free(inB); free(dist); free(queue); free(ball);
+        return -1;
+    }
+    for (size_t i = 0; i < N; i++) { alive[i] = 1; dist[i] = -1; }
+    /* Algorithm 5, lines 1-4: exact h-degrees, the sampled counts and rates */
+    for (int32_t v = 0; v < n; v++) {
+        int64_t len = 0;
+        d0[v] = (int32_t)bfs_count(v, h, row_ptr, col, alive, dist, queue, ball, &len);
+        int64_t c = 0;
+        for (int64_t i = 0; i < len; i++) c += in_s[ball[i]] ? 1 : 0;
+        sel[v] = sel0[v] = c;
+    }
+    for (int32_t v = 0; v < n; v++) {
+        est[v] = d0[v] == 0 ? 0 : sampled_estimate(sel[v], sel0[v], d0[v], d0[v]);
+        if (est_init_out) est_init_out[v] = est[v];
+    }
+    /* lines 5-7: Algorithm 2 on the estimates */
+    int32_t k = 0;
+    int64_t removed = 0;
+    while (removed < n) {
+        int32_t m = -1;
+        for (int32_t u = 0; u < n; u++)
+            if (alive[u] && (m < 0 || est[u] < m)) m = est[u];
+        if (m > k) k = m;
+        for (int32_t u = 0; u < n; u++)
+            if (alive[u] && est[u] <= k) inB[u] = 1;
+        for (;;) {
+            int32_t v = -1;
+            for (int32_t u = 0; u < n; u++)
+                if (inB[u]) { v = u; break; }
+            if (v < 0) break;
+            inB[v] = 0;
+            core_out[v] = k;
+            removed++;
+            if (sampled_update(n, row_ptr, col, alive, in_s, h, v, sel, sel0, d0, est) < 0) {
+                free(d0); free(est); free(sel); free(sel0); free(alive); free(inB); free(dist); free(queue);
+                free(ball);
+                return -1;
+            }
+            alive[v] = 0;
+            for (int32_t u = 0; u < n; u++)
+                if (alive[u] && !inB[u] && est[u] <= k) inB[u] = 1;
+        }
+    }
+    free(d0); free(est); free(sel); free(sel0); free(alive); free(inB); free(dist); free(queue); free(ball);
+    return 0;
+}
+
+/* The estimator alone (for the pins): floor(sel * d0 / sel0). */
+int32_t orc_sampled_estimate(int64_t sel, int64_t sel0, int64_t d0) { return sampled_estimate(sel, sel0, d0, -1); }
 
 /* ------------------------------------------------------------------------ */
 /* Definition 2 by exhaustion, for n <= 24: adj[v] is v's neighbour bitmask.  */
