@@ -12,6 +12,8 @@ Functions (each follows the passage named in oracle.c):
   kcore_bz(g)                         h = 1: Batagelj-Zaversnik k-core (Sec. II)
   certificate(g, h, core, rnd, verts) exactness certificate for a claimed
                                       core index and peel round
+  certificate_all(g, h, core, rnd)    the same on every vertex, early-stopped
+                                      BFS (full-size graphs)
 """
 from __future__ import annotations
 
@@ -65,6 +67,8 @@ def _load():
         lib.orc_kcore_bz.restype = ctypes.c_int
         lib.orc_certificate.argtypes = [i32, P, P, i32, P, P, i64, P, P]
         lib.orc_certificate.restype = ctypes.c_int64
+        lib.orc_certificate_all.argtypes = [i32, P, P, i32, P, P, i32, i32, P]
+        lib.orc_certificate_all.restype = ctypes.c_int64
         lib.orc_bitmap_update.argtypes = [i32, P, P, P, i32, i32, P, P, i64, P]
         lib.orc_bitmap_update.restype = ctypes.c_int64
         lib.orc_peel_bitmap.argtypes = [i32, P, P, i32, P, P]
@@ -254,6 +258,25 @@ def certificate(g, h: int, core, rnd, verts=None):
     if rc == -2:
         raise ValueError("negative core or round value")
     return int(rc), bad[: len(v)]
+
+
+def certificate_all(g, h: int, core, rnd, small_cap: int = 1024, words: int = 8):
+    """The certificate of `certificate` on every vertex (full-size graphs):
+    vertices with core <= small_cap by one early-stopped BFS each, the others
+    by a bit-parallel BFS of 64*words sources. Returns (failures, per-vertex
+    bad mask: 1 = (i) failed, 2 = (ii) failed)."""
+    lib = _load()
+    rp, col = _csr(g)
+    c = np.ascontiguousarray(core, dtype=np.int32)
+    r = np.ascontiguousarray(rnd, dtype=np.int32)
+    bad = np.zeros(max(g.n, 1), dtype=np.int32)
+    rc = lib.orc_certificate_all(g.n, _p(rp), _p(col), int(h), _p(c), _p(r), int(small_cap), int(words),
+                                  _p(bad))
+    if rc == -1:
+        raise MemoryError("oracle: out of memory")
+    if rc == -2:
+        raise ValueError("negative core or round value")
+    return int(rc), bad[: g.n]
 
 
 def level_rounds(g, h: int, core):

@@ -32,6 +32,8 @@
  *   orc_certificate   checks a claimed core index c and peel round r against
  *                     two inequalities that together imply c is exact (the
  *                     argument is written above the function).
+ *   orc_certificate_all  the same check on every vertex, each BFS stopped as
+ *                     soon as its inequality is decided (full-size graphs).
  *
  * Readings of the paper taken here:
  *   - k starts at 0, so isolated vertices get core index 0 (Algorithm 1 starts
@@ -745,6 +747,280 @@ int64_t orc_certificate(int32_t n, const int32_t *row_ptr, const int32_t *col,
         free(dist); free(queue); free(mask);
     }
     if (err) return -1;
+    return fails + f2;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The same certificate on EVERY vertex, fast enough for the 1e6-vertex      */
+/* graphs. Conditions (0), (i) and (ii) are exactly those of                  */
+/* orc_certificate; what changes is how the BFS counts are taken:             */
+/*  - the vertex set of each BFS ({c >= c[v]} for (i), {r >= r[v]} for (ii))  */
+/*    is tested on the fly from c[] and r[] (no n-byte mask per vertex);      */
+/*  - a vertex with c[v] <= small_cap runs its own BFS, stopped as soon as    */
+/*    the inequality is decided ((i) holds once c[v] other vertices are       */
+/*    reached, (ii) fails once c[v] + 1 are);                                 */
+/*  - the other vertices are checked 64*W at a time by a bit-parallel BFS:   */
+/*    bit j of a vertex's W words stands for source j of the batch. For one  */
+/*    condition the sources are sorted by key (c or r), so that a vertex u   */
+/*    belongs to source j's subgraph {key >= key[s_j]} exactly for the first */
+/*    acc(u) sources of the batch, acc(u) = |{j : key[s_j] <= key[u]}|; u    */
+/*    carries and passes on only those bits.                                 */
+/* Returns the number of failed checks (0 = pass), -1 on ENOMEM, -2 on a    */
+/* negative value; bad_out (nullable, int32[n]) as for orc_certificate.     */
+/* ------------------------------------------------------------------------ */
+
+/* BFS from v to radius h inside {u : key[u] >= key[v]}; stops once `cap`    */
+/* other vertices are reached. Returns min(reached, cap). dist[] all -1 on   */
+/* entry and on return.                                                      */
+static int64_t bfs_count_capped(int32_t v, int32_t h, const int32_t *row_ptr, const int32_t *col,
+                                const int32_t *key, int64_t cap, int32_t *dist, int32_t *queue)
+{
+    const int32_t kv = key[v];
+    int64_t head = 0, tail = 0, reached = 0;
+    queue[tail++] = v;
+    dist[v] = 0;
+    while (head < tail && reached < cap) {
+        int32_t x = queue[head++];
+        if (dist[x] == h) continue;
+        for (int32_t e = row_ptr[x]; e < row_ptr[x + 1] && reached < cap; e++) {
+            int32_t y = col[e];
+            if (key[y] < kv || dist[y] >= 0) continue; /* outside the subgraph, or seen */
+            dist[y] = dist[x] + 1;
+            queue[tail++] = y;
+            reached++;
+        }
+    }
+    for (int64_t i = 0; i < tail; i++) dist[queue[i]] = -1;
+    return reached;
+}
+
+static const int32_t *g_sort_key; /* qsort has no context argument */
+static int cmp_by_key(const void *a, const void *b)
+{
+    const int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    const int32_t kx = g_sort_key[x], ky = g_sort_key[y];
+    if (kx != ky) return (kx > ky) - (kx < ky);
+    return (x > y) - (x < y);
+}
+
+/* Bits of word k (sources 64k .. 64k+63) that stand for the first a sources. */
+static uint64_t prefix_bits(int64_t a, int k)
+{
+    const int64_t lo = 64 * (int64_t)k;
+    if (a >= lo + 64) return ~0ull;
+    if (a <= lo) return 0ull;
+    return (1ull << (a - lo)) - 1ull;
+}
+
+/* Adds the byte-sliced column counts sl (W words x 8 slices) into lc and
+ * clears them: byte b of slice t of word k counts column 64k + 8b + t. */
+static void slice_flush(uint64_t *sl, int64_t *lc, int W)
+{
+    for (int k = 0; k < W; k++)
+        for (int t = 0; t < 8; t++) {
+            uint64_t v = sl[8 * k + t];
+            for (int b = 0; b < 8; b++) lc[64 * k + 8 * b + t] += (int64_t)((v >> (8 * b)) & 0xffu);
+            sl[8 * k + t] = 0;
+        }
+}
+
+/* One condition (cond 1: count >= c[s]; cond 2: count <= c[s]) for the
+ * sources srcs[0..ns), sorted by key, 64*W per batch. */
+static int bits_condition(int32_t n, const int32_t *rp, const int32_t *col, int32_t h, const int32_t *key,
+                          const int32_t *c, const int32_t *srcs, int64_t ns, int cond, int W,
+                          int32_t *bad_out)
+{
+    const int64_t B = 64 * (int64_t)W;
+    const size_t words = (size_t)n * (size_t)W;
+    uint64_t *V = malloc(sizeof(uint64_t) * words);
+    uint64_t *F = malloc(sizeof(uint64_t) * words);
+    uint64_t *N = malloc(sizeof(uint64_t) * words);
+    uint8_t *fl = malloc((size_t)n), *fn = malloc((size_t)n);
+    int32_t *acc = malloc(sizeof(int32_t) * (size_t)n);
+    int64_t *cnt = malloc(sizeof(int64_t) * (size_t)B);
+    if (!V || !F || !N || !fl || !fn || !acc || !cnt) {
+        free(V); free(F); free(N); free(fl); free(fn); free(acc); free(cnt);
+        return -1;
+    }
+    int oom = 0;
+    for (int64_t b0 = 0; b0 < ns && !oom; b0 += B) {
+        const int64_t nb = ns - b0 < B ? ns - b0 : B;
+        const int32_t *bs = srcs + b0;
+        const int32_t kmin = key[bs[0]], kmax = key[bs[nb - 1]];
+#pragma omp parallel for schedule(static)
+        for (int32_t u = 0; u < n; u++) {
+            const int32_t ku = key[u];
+            int64_t a;
+            if (ku < kmin) a = 0;
+            else if (ku >= kmax) a = nb;
+            else { /* first batch position whose key exceeds ku */
+                int64_t lo = 0, hi = nb;
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi) / 2;
+                    if (key[bs[mid]] <= ku) lo = mid + 1; else hi = mid;
+                }
+                a = lo;
+            }
+            acc[u] = (int32_t)a;
+            for (int k = 0; k < W; k++) V[(size_t)u * W + k] = F[(size_t)u * W + k] = 0;
+            fl[u] = 0;
+        }
+        for (int64_t j = 0; j < nb; j++) {
+            const int32_t s = bs[j];
+            V[(size_t)s * W + j / 64] |= 1ull << (j % 64);
+            F[(size_t)s * W + j / 64] |= 1ull << (j % 64);
+            fl[s] = 1;
+        }
+        for (int64_t j = 0; j < B; j++) cnt[j] = 0;
+        for (int32_t lvl = 1; lvl <= h; lvl++) {
+#pragma omp parallel
+            {
+                /* column counts: byte t of sl[8k + t'] counts bit 8t + t' of
+                 * word k over the words added; flushed every 255 adds */
+                int64_t *lc = calloc((size_t)B, sizeof(int64_t));
+                uint64_t *sl = calloc((size_t)W * 8, sizeof(uint64_t));
+                int adds = 0;
+                uint64_t x[64];
+                if (!lc || !sl) {
+#pragma omp atomic write
+                    oom = 1;
+                }
+#pragma omp for schedule(dynamic, 1024)
+                for (int32_t u = 0; u < n; u++) {
+                    fn[u] = 0;
+                    if (oom) continue;
+                    const int32_t a = acc[u];
+                    if (a == 0) continue;
+                    int any = 0;
+                    for (int k = 0; k < W; k++) x[k] = 0;
+                    for (int32_t e = rp[u]; e < rp[u + 1]; e++) {
+                        const int32_t w = col[e];
+                        if (!fl[w]) continue;
+                        for (int k = 0; k < W; k++) x[k] |= F[(size_t)w * W + k];
+                    }
+                    for (int k = 0; k < W; k++) {
+                        x[k] &= ~V[(size_t)u * W + k] & prefix_bits(a, k);
+                        any |= x[k] != 0;
+                    }
+                    if (!any) continue;
+                    fn[u] = 1;
+                    for (int k = 0; k < W; k++) {
+                        N[(size_t)u * W + k] = x[k];
+                        V[(size_t)u * W + k] |= x[k];
+                        for (int t = 0; t < 8; t++) sl[8 * k + t] += (x[k] >> t) & 0x0101010101010101ull;
+                    }
+                    if (++adds == 255) {
+                        slice_flush(sl, lc, W);
+                        adds = 0;
+                    }
+                }
+                if (lc && sl) {
+                    slice_flush(sl, lc, W);
+#pragma omp critical
+                    for (int64_t j = 0; j < B; j++) cnt[j] += lc[j];
+                }
+                free(lc);
+                free(sl);
+            }
+            if (oom) break;
+            uint64_t *t = F; F = N; N = t;
+            uint8_t *tf = fl; fl = fn; fn = tf;
+        }
+        for (int64_t j = 0; j < nb; j++) {
+            const int32_t s = bs[j];
+            if (cond == 1 ? (cnt[j] < c[s]) : (cnt[j] > c[s])) bad_out[s] |= cond;
+        }
+    }
+    free(V); free(F); free(N); free(fl); free(fn); free(acc); free(cnt);
+    return oom ? -1 : 0;
+}
+
+int64_t orc_certificate_all(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                            int32_t h, const int32_t *c, const int32_t *r, int32_t small_cap, int32_t W,
+                            int32_t *bad_out)
+{
+    int64_t fails = 0;
+    if (n == 0) return 0;
+    if (W < 1 || W > 64) return -2;
+    /* (0) */
+    int32_t rmax = 0;
+    for (int32_t v = 0; v < n; v++) {
+        if (r[v] < 0 || c[v] < 0) return -2;
+        if (r[v] > rmax) rmax = r[v];
+    }
+    int32_t *cr = malloc(sizeof(int32_t) * ((size_t)rmax + 1));
+    if (!cr) return -1;
+    for (int32_t i = 0; i <= rmax; i++) cr[i] = -1;
+    for (int32_t v = 0; v < n; v++) {
+        if (cr[r[v]] < 0) cr[r[v]] = c[v];
+        else if (cr[r[v]] != c[v]) fails++;
+    }
+    int32_t last = -1;
+    for (int32_t i = 0; i <= rmax; i++) {
+        if (cr[i] < 0) continue;
+        if (cr[i] < last) fails++;
+        last = cr[i];
+    }
+    free(cr);
+    int32_t *bad_mem = NULL;
+    if (!bad_out) {
+        bad_mem = malloc(sizeof(int32_t) * (size_t)n);
+        if (!bad_mem) return -1;
+        bad_out = bad_mem;
+    }
+    for (int32_t v = 0; v < n; v++) bad_out[v] = 0;
+
+    /* vertices with a small claimed core: one early-stopped BFS each */
+    int64_t f2 = 0;
+    int err = 0;
+#pragma omp parallel reduction(+ : f2)
+    {
+        int32_t *dist = malloc(sizeof(int32_t) * (size_t)n);
+        int32_t *queue = malloc(sizeof(int32_t) * (size_t)n);
+        if (!dist || !queue) {
+#pragma omp atomic write
+            err = 1;
+        } else {
+            for (int32_t i = 0; i < n; i++) dist[i] = -1;
+#pragma omp for schedule(dynamic, 256)
+            for (int32_t v = 0; v < n; v++) {
+                if (c[v] > small_cap) continue;
+                int32_t bad = 0;
+                /* (i): at least c[v] others within h in G[{c >= c[v]}] */
+                if (bfs_count_capped(v, h, row_ptr, col, c, c[v], dist, queue) < c[v]) bad |= 1;
+                /* (ii): at most c[v] others within h in G[{r >= r[v]}] */
+                if (bfs_count_capped(v, h, row_ptr, col, r, (int64_t)c[v] + 1, dist, queue) > c[v]) bad |= 2;
+                bad_out[v] = bad;
+            }
+        }
+        free(dist); free(queue);
+    }
+    if (err) { free(bad_mem); return -1; }
+
+    /* the others: bit-parallel, 64*W sources per BFS, one pass per condition */
+    int64_t ns = 0;
+    for (int32_t v = 0; v < n; v++) ns += c[v] > small_cap;
+    if (ns > 0) {
+        int32_t *srcs = malloc(sizeof(int32_t) * (size_t)ns);
+        if (!srcs) { free(bad_mem); return -1; }
+        for (int cond = 1; cond <= 2; cond++) {
+            const int32_t *key = cond == 1 ? c : r;
+            int64_t i = 0;
+            for (int32_t v = 0; v < n; v++)
+                if (c[v] > small_cap) srcs[i++] = v;
+            g_sort_key = key;
+            qsort(srcs, (size_t)ns, sizeof(int32_t), cmp_by_key);
+            if (bits_condition(n, row_ptr, col, h, key, c, srcs, ns, cond, W, bad_out) < 0) {
+                free(srcs);
+                free(bad_mem);
+                return -1;
+            }
+        }
+        free(srcs);
+    }
+    /* a vertex failing both conditions counts once, as in orc_certificate */
+    for (int32_t v = 0; v < n; v++) f2 += bad_out[v] != 0;
+    free(bad_mem);
     return fails + f2;
 }
 

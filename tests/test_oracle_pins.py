@@ -45,6 +45,18 @@ def test_fig1_core_h2_matches_example1(fig1):
     assert (oracle.bruteforce(g, 2) == want).all()
 
 
+def test_fig1_level_rounds_match_example2_order(fig1):
+    # the level-synchronous round sequence (4:{v1}) (4:{v2,v3}) (5:{v5})
+    # (5:{v4,v6}) (5:{v7}) (6:{v8..v14}), derived by hand in the golden file
+    g, vals = fig1
+    want = np.array([int(x) for x in vals["rounds_h2"]])
+    core = np.array([int(x) for x in vals["core_h2"]])
+    rnd = oracle.level_rounds(g, 2, core)
+    assert np.array_equal(rnd, want)
+    # and the certificate accepts exactly this pair
+    assert oracle.certificate(g, 2, core, rnd)[0] == 0
+
+
 def test_fig1_core_h1_is_2_everywhere(fig1):
     g, vals = fig1
     want = np.array([int(x) for x in vals["core_h1"]])
@@ -244,6 +256,71 @@ def test_certificate_accepts_true_and_rejects_mutations():
                 r2[late] = 0
                 c2 = c.copy()
                 assert oracle.certificate(g, h, c2, r2)[0] > 0
+
+
+def _mutations(c, r, seed):
+    """Claimed (core, round) pairs that are wrong in the ways a kernel could
+    be: one value off by one, a uniform shift, a random vertex's round moved,
+    two vertices' cores swapped."""
+    rng = np.random.default_rng(seed)
+    out = []
+    v = int(rng.integers(len(c)))
+    for delta in (+1, -1):
+        c2 = c.copy()
+        c2[v] = max(0, c2[v] + delta)
+        out.append((c2, r))
+    out.append((c + 1, r))
+    out.append((np.maximum(c - 1, 0), r))
+    r2 = r.copy()
+    r2[v] = int(rng.integers(r.max() + 1))
+    out.append((c, r2))
+    a, b = rng.integers(len(c), size=2)
+    c3 = c.copy()
+    c3[a], c3[b] = c3[b], c3[a]
+    out.append((c3, r))
+    return out
+
+
+# both paths of certificate_all: every vertex by its own early-stopped BFS
+# (small_cap large), every vertex bit-parallel (small_cap -1) with one-word
+# and two-word batches (several batches, a ragged last one), and a mix
+PATHS = [(10 ** 9, 8), (-1, 1), (-1, 2), (3, 1)]
+
+
+def test_certificate_all_agrees_with_per_vertex_certificate():
+    # the all-vertex check makes the same per-vertex decisions as the plain
+    # per-vertex one, on true results and on every mutation, on every path
+    for i, g in enumerate(small_graphs(510, 9, (8, 150))):
+        for h in [1, 2, 3, 4]:
+            c = oracle.peel(g, h)
+            r = oracle.level_rounds(g, h, c)
+            for cap, w in PATHS:
+                assert oracle.certificate_all(g, h, c, r, cap, w)[0] == 0, (g.name, h, cap, w)
+            for c2, r2 in _mutations(c, r, 100 * i + h):
+                fp, bp = oracle.certificate(g, h, c2, r2)
+                for cap, w in PATHS:
+                    fa, ba = oracle.certificate_all(g, h, c2, r2, cap, w)
+                    assert fa == fp and np.array_equal(ba, bp), (g.name, h, cap, w)
+                if not (np.array_equal(c2, c)):
+                    assert fp > 0, (g.name, h)
+
+
+def test_certificate_all_on_a_chung_lu_graph_with_hubs():
+    # hubs make long rows and large balls: the early stop must not change a
+    # decision
+    g = gg.chung_lu(1500, 8.0, 2.3, 200.0, 91)
+    for h in (2, 3):
+        c = oracle.peel(g, h)
+        r = oracle.level_rounds(g, h, c)
+        c2 = c.copy()
+        top = np.flatnonzero(c == c.max())
+        c2[top[0]] += 1
+        fp, bp = oracle.certificate(g, h, c2, r)
+        assert fp > 0
+        for cap, w in PATHS + [(int(np.median(c)), 4)]:
+            assert oracle.certificate_all(g, h, c, r, cap, w)[0] == 0
+            fa, ba = oracle.certificate_all(g, h, c2, r, cap, w)
+            assert fa == fp and np.array_equal(ba, bp)
 
 
 def test_certificate_rejects_uniform_shift():
