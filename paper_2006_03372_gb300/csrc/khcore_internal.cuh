@@ -7,6 +7,16 @@
 
 namespace khc {
 
+// One CSR row [lo, hi) of an array of m entries is well formed when
+// 0 <= lo <= hi <= m. Taken in 64 bits, so that the difference of two int32
+// offsets cannot wrap (offsets 2^31 - 1 followed by -2 would give a positive
+// int32 row length). Host-side validation and the device-side check of the
+// allocation-free entry point use this same predicate.
+__host__ __device__ __forceinline__ bool csr_row_ok(int64_t lo, int64_t hi, int64_t m)
+{
+    return 0 <= lo && lo <= hi && hi <= m;
+}
+
 // Threads per block of the BFS and peel kernels.
 constexpr int kBlock = 512;
 // Degree classes of the pull expansion: a vertex with deg <= kLightMax is

@@ -19,7 +19,9 @@ khcore_status set_thread_error(khcore_status s, const char *fmt, ...);  // khcor
 
 namespace {
 
-// Every device that loads the library holds this array until the process exits.
+// A device holds this array from the first load of the library's device code
+// on it (the first call here, under lazy module loading) until the process
+// exits.
 constexpr size_t kStaticScratchBytes = size_t(32) << 20;
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
@@ -91,9 +93,10 @@ __global__ void k_static_check(int32_t n, int64_t m, const int32_t *rp, const in
     int32_t c[3] = {0, 0, 0};
     if (t0 == 0 && (rp[0] != 0 || (int64_t)rp[n] != m)) err |= 1;
     for (int64_t v = t0; v < n; v += stride) {
-        const int32_t d = rp[v + 1] - rp[v];
-        if (d < 0) err |= 1;
-        c[degree_class(d)]++;
+        const int64_t lo = rp[v], hi = rp[v + 1];
+        if (!csr_row_ok(lo, hi, m)) err |= 1;
+        const int64_t d = hi - lo;
+        c[degree_class(d < 0 ? 0 : (int32_t)min(d, (int64_t)INT32_MAX))]++;
     }
     for (int64_t e = t0; e < m; e += stride) {
         const int32_t x = col[e];
@@ -139,6 +142,8 @@ DeviceSlot g_slots[kMaxDevices];
 
 // Once per device, with that device current: the device address of the
 // scratch array (its host-side name is only a stand-in) and the BFS grid.
+// The address is cached per device ordinal for the life of the process, which
+// is why cudaDeviceReset between calls is not supported.
 cudaError_t device_slot(int dev, DeviceSlot *out)
 {
     std::lock_guard<std::mutex> lock(g_slot_mu);

@@ -59,7 +59,7 @@ def _create_status(n, rp, col):
     return 0, ""
 
 
-@pytest.mark.parametrize("case", ["selfloop", "dup", "asym", "range", "rowptr", "neg_n"])
+@pytest.mark.parametrize("case", ["selfloop", "dup", "asym", "range", "rowptr", "neg_n", "rowptr_wrap"])
 def test_malformed_csr_is_einval(lib, case):
     g = gg.cycle(6)
     rp, col, n = g.row_ptr.copy(), g.col.copy(), g.n
@@ -76,6 +76,12 @@ def test_malformed_csr_is_einval(lib, case):
         rp[3] = rp[2] - 1
     elif case == "neg_n":
         n = -1
+    elif case == "rowptr_wrap":
+        # offsets whose int32 differences wrap to non-negative row lengths:
+        # 2^31 - 1 followed by -2 (csr_row_ok takes them in 64 bits)
+        n = 3
+        rp = np.array([0, 2 ** 31 - 1, -2, 4], dtype=np.int32)
+        col = np.array([1, 0, 2, 1], dtype=np.int32)
     st, msg = _create_status(n, rp, col)
     assert st == 1, msg
 
