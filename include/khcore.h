@@ -27,6 +27,12 @@
  * A CUDA error leaves the context failed: later calls on it return
  * KHCORE_ECUDA, and the context may only be destroyed.
  *
+ * Fault injection (testing). If the environment variable KHCORE_FAIL_ALLOC_AT
+ * holds N > 0 when a context is created, the N-th device allocation the
+ * creating thread makes from then on fails as if the device were full (no
+ * cudaMalloc is called for it): the call that made it returns KHCORE_ENOMEM
+ * and releases whatever it had allocated. Unset or 0 turns this off.
+ *
  * Threads and streams. A context belongs to one host thread at a time. All
  * of its device work is ordered on the stream given to khcore_create. The
  * calls return after their outputs are written (host outputs are complete;
@@ -154,8 +160,11 @@ khcore_status khcore_hdegrees_of(khcore_ctx *ctx, int32_t h, int32_t count, cons
  * inside a host process that owns all device memory through its own pool and
  * hands it only input and output buffers, or a latency-bound path that cannot
  * take cudaMalloc's device-wide synchronisation. The BFS scratch comes from a
- * fixed 32 MiB array in the library's device image, which every device that
- * loads the library holds until the process exits. This call allocates
+ * fixed 32 MiB array in the library's device image. A device holds that array
+ * from the moment the library's device code is loaded on it until the process
+ * exits; under CUDA's default lazy module loading that is the first call of
+ * this entry point on the device, so make that first call during the caller's
+ * set-up, where acquiring device memory is still allowed. This call allocates
  * nothing (no cudaMalloc, cudaFree or allocating library routine); it only
  * copies four status words to a host stack buffer and synchronises `stream`
  * once after its checks and once before returning.
@@ -178,8 +187,10 @@ khcore_status khcore_hdegrees_of(khcore_ctx *ctx, int32_t h, int32_t count, cons
  * range and repeated listed ids are found on the device and also return
  * KHCORE_EINVAL. Messages: khcore_last_error(NULL), per host thread.
  * Set-up: the first call on a device, with that device current, looks up
- * the array's device address (cudaGetSymbolAddress) and caches it; make that
- * first call before any stream capture begins.
+ * the array's device address (cudaGetSymbolAddress) and caches it for that
+ * device ordinal; make that first call before any stream capture begins.
+ * cudaDeviceReset between calls is not supported: it discards the device's
+ * copy of the array, and the cached address would then be stale.
  * Sharing: every call on a device uses the same array, and each call clears
  * the parts that must start at zero. Calls whose device work overlaps (two
  * host threads, or two streams, on one device) race on the array and give

@@ -153,11 +153,28 @@ bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Allocation-failure injection for tests, entirely on the host: when the
+// environment variable KHCORE_FAIL_ALLOC_AT holds N > 0 as a context is
+// created, the N-th device allocation the calling thread makes from then on
+// (the context's own buffers first, then the BFS rows its first decomposition
+// allocates) fails as if the device were out of memory, without calling
+// cudaMalloc. Unset or 0: no injection.
+thread_local int64_t g_fail_alloc_at = 0;
+thread_local int64_t g_allocs_seen = 0;
+
+void arm_alloc_injection()
+{
+    const char *e = getenv("KHCORE_FAIL_ALLOC_AT");
+    g_fail_alloc_at = e ? atoll(e) : 0;
+    g_allocs_seen = 0;
+}
+
 template <class T>
 cudaError_t dev_alloc(T **p, size_t count)
 {
     *p = nullptr;
     if (count == 0) count = 1;
+    if (g_fail_alloc_at > 0 && ++g_allocs_seen == g_fail_alloc_at) return cudaErrorMemoryAllocation;
     return cudaMalloc((void **)p, count * sizeof(T));
 }
 
@@ -183,8 +200,9 @@ bool validate_csr(int32_t n, const std::vector<int32_t> &rp, const std::vector<i
         return false;
     }
     for (int32_t v = 0; v < n; v++)
-        if (rp[v + 1] < rp[v]) {
-            snprintf(buf, sizeof buf, "row_ptr decreases at vertex %d", v);
+        if (!csr_row_ok(rp[v], rp[v + 1], rp[n])) {
+            snprintf(buf, sizeof buf, "row_ptr is not a CSR offset array at vertex %d (it decreases or leaves [0, %d])",
+                     v, rp[n]);
             msg = buf;
             return false;
         }
@@ -962,6 +980,7 @@ khcore_status create_common(int32_t G, const std::vector<int64_t> &v_off, std::v
                             std::vector<int32_t> &cl, const std::vector<int32_t> *gid, void *stream,
                             khcore_ctx **out)
 {
+    arm_alloc_injection();
     khcore_ctx *c = new (std::nothrow) khcore_ctx();
     if (!c) return fail(nullptr, KHCORE_ENOMEM, "host allocation failed");
     c->n = (int32_t)v_off[G];
