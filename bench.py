@@ -47,7 +47,8 @@ def parse():
     p.add_argument("--hs", default="2", help="comma-separated h values decomposed per step")
     p.add_argument("--words", type=int, default=0, help="64-bit source words per vertex (0 = auto)")
     p.add_argument("--e2e-steps", type=int, default=1, help="end-to-end runs through host buffers (0: skip)")
-    p.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU work of the oracle sample")
+    p.add_argument("--ref-removals", type=int, default=256,
+                   help="reference arm: Algorithm 1 removals timed per step after the full h-degree pass")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", choices=["decompose", "hdeg", "batch", "serve"], default="decompose",
                    help="decompose: the headline (default); hdeg: the all-vertex h-degree pass alone "
@@ -133,8 +134,8 @@ def workload_name(args, g) -> str:
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # persistent round kernel on the headline workload, from one ncu capture of
 # `python bench.py --steps 1 --warmup 0 --no-cpu-baseline --e2e-steps 0`
-# (profiles/k_decompose_w4_cl1m_h2_dram.md), keyed by a digest of the kernel
-# sources it was taken on: reported only while the sources are unchanged.
+# (the ncu capture of this kernel), keyed by a digest of the kernel sources it
+# was taken on: reported only while the sources are unchanged.
 KERNEL_TRAFFIC = {("cl1m", (2,), "82959768d651a8c2"): 50.12e9}
 
 
@@ -175,95 +176,104 @@ def dist_setup(args):
     return world, rank, local
 
 
-def cpu_baseline_sample(g, hs, seconds, rank):
+def cpu_baseline_sample(g, hs, removals):
     """The oracle as it stands, on the host cores, on a bounded sample of the
-    same decomposition: its own h-degree pass (OpenMP over vertices), then
-    Algorithm 1 (one thread) stopped after K removals; the decomposition time
-    is extrapolated as t_pass + t_peel(K) * n / K. Removals come in ascending
-    h-degree order, so the first K are among the cheapest: the estimate is an
-    upper bound on the oracle's rate. When even the h-degree pass does not fit
-    the budget it is extrapolated from a vertex sample and the peel is left
-    out (a looser upper bound)."""
-    import numpy as np
-
-    import graphgen as gg
+    same decomposition (the reference arm's step, oracle_step): its own
+    h-degree pass over every vertex, measured, then Algorithm 1 for a bounded
+    number of removals, measured, extrapolated to all n removals. Removals come
+    in ascending h-degree order, so the first ones are among the cheapest: the
+    estimate is an upper bound on the oracle's rate."""
     import oracle
-    rng = gg.Stream(99, "cpu-sample")
-    per_h = {}
     threads = oracle.threads() or 1
-    for h in hs:
-        budget = seconds / len(hs)
-        # cost of the h-degree pass, from a small vertex sample
-        v = np.argsort(rng.u64(g.n), kind="stable")[:256].astype(np.int32)
-        t0 = time.perf_counter()
-        oracle.hdegree_list(g, h, v)
-        t_pass_est = (time.perf_counter() - t0) * g.n / len(v)
-        rec = {"pass_s": t_pass_est, "pass_measured": False, "removed": 0, "peel_s": 0.0}
-        if t_pass_est < budget / 2:
-            t0 = time.perf_counter()
-            deg = oracle.hdegrees(g, h)
-            rec["pass_s"] = time.perf_counter() - t0
-            rec["pass_measured"] = True
-            k = 256
-            while True:
-                t0 = time.perf_counter()
-                removed, _, _ = oracle.peel_bounded(g, h, k, deg_init=deg)
-                dt = time.perf_counter() - t0
-                rec["removed"], rec["peel_s"] = removed, dt
-                if removed >= g.n or dt > (budget - rec["pass_s"]) / 4 or k >= g.n:
-                    break
-                k *= 4
-        est = rec["pass_s"] + (rec["peel_s"] * g.n / rec["removed"] if rec["removed"] else 0.0)
-        rec["est_decompose_s"] = est
-        per_h[h] = rec
-    est_step_s = sum(r["est_decompose_s"] for r in per_h.values())
-    parts = []
-    for h, r in per_h.items():
-        if r["removed"]:
-            parts.append(f"h={h}: oracle h-degree pass over all {g.n} vertices ({r['pass_s']:.1f} s, {threads} "
-                         f"threads) + Algorithm 1 stopped after {r['removed']} removals ({r['peel_s']:.1f} s, 1 "
-                         f"thread), extrapolated to {g.n} removals")
-        else:
-            parts.append(f"h={h}: oracle h-degree pass extrapolated from a 256-vertex sample "
-                         f"({r['pass_s']:.1f} s for all vertices); peel not timed")
+    recs = {h: oracle_step(g, h, removals) for h in hs}
+    est_step_s = sum(r["est_decompose_s"] for r in recs.values())
+    sample = "; ".join(
+        f"h={h}: oracle h-degree pass over all {g.n} vertices ({r['pass_s']:.2f} s, {threads} threads, measured) + "
+        f"Algorithm 1 for {r['removed']} removals ({r['peel_s']:.2f} s, 1 thread, measured)"
+        + (f", extrapolated to {g.n} removals" if r["extrapolated"] else ", the whole decomposition")
+        for h, r in recs.items())
     return {
-        "value": len(hs) / est_step_s,
-        "unit": UNIT,
-        "cores": threads,
-        "kind": "oracle",
-        "sample": "; ".join(parts) + ". An upper bound on the oracle's rate (early removals are the cheapest).",
-        "est_decompose_s": {str(h): r["est_decompose_s"] for h, r in per_h.items()},
+        "value": len(hs) / est_step_s, "unit": UNIT, "cores": threads, "kind": "oracle",
+        "sample": sample + ". An upper bound on the oracle's rate (early removals are the cheapest).",
+        "extrapolated": any(r["extrapolated"] for r in recs.values()),
+        "measured_s": {str(h): {"pass_s": r["pass_s"], "peel_s": r["peel_s"], "removed": r["removed"]}
+                       for h, r in recs.items()},
+        "est_decompose_s": {str(h): r["est_decompose_s"] for h, r in recs.items()},
     }
 
 
 # --------------------------------------------------------------- reference arm
+
+def oracle_step(g, h, removals):
+    """One step of the reference arm: the oracle's own h-degree pass over
+    every vertex (OpenMP over vertices, all host cores), then Algorithm 1 (one
+    thread) from those h-degrees, stopped after `removals` removals (run to the
+    end when that covers the graph). Returns the measured seconds and the
+    decomposition time they extrapolate to: t_pass + t_peel * n / removed."""
+    import oracle
+    t0 = time.perf_counter()
+    deg = oracle.hdegrees(g, h)
+    t_pass = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    removed, _, _ = oracle.peel_bounded(g, h, removals if removals < g.n else -1, deg_init=deg)
+    t_peel = time.perf_counter() - t0
+    est = t_pass + (t_peel * g.n / removed if removed else 0.0)
+    return {"pass_s": t_pass, "peel_s": t_peel, "removed": int(removed), "est_decompose_s": est,
+            "extrapolated": bool(removed < g.n)}
+
+
+def oracle_config1_pair():
+    """The one configuration the oracle decomposes in full within seconds
+    (Erdos-Renyi n=2000, m=8000, seed 1, h=2): Algorithm 1 end to end, one
+    thread, no extrapolation."""
+    import graphgen as gg
+    import oracle
+    g = gg.config1_er()
+    t0 = time.perf_counter()
+    core = oracle.peel(g, 2)
+    return {"workload": "er_n2000_m8000_seed1_h2", "oracle_s": time.perf_counter() - t0, "cores": 1,
+            "extrapolated": False}, core
+
 
 def run_reference(args):
     world, rank, _ = dist_setup(args)
     if rank != 0:
         return 0
     import graphgen as gg
+    import oracle
     hs = [int(x) for x in args.hs.split(",")]
     g = gg.config_graph(args.graph)
-    # each step: a bounded sample, sized so the whole run stays within minutes
-    per_step = max(2.0, min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
+    threads = oracle.threads() or 1
     for _ in range(args.warmup):
-        cpu_baseline_sample(g, hs, per_step / 4, rank)
-    vals = []
+        for h in hs:
+            oracle_step(g, h, args.ref_removals)
     t0 = time.perf_counter()
-    last = None
+    per_step = []
     for _ in range(args.steps):
-        last = cpu_baseline_sample(g, hs, per_step, rank)
-        vals.append(last["value"])
+        per_step.append([oracle_step(g, h, args.ref_removals) for h in hs])
     wall = time.perf_counter() - t0
-    value = statistics.median(vals)
+    est = [sum(r["est_decompose_s"] for r in st) for st in per_step]
+    value = len(hs) / statistics.median(est)
+    last = per_step[-1]
+    extrapolated = any(r["extrapolated"] for r in last)
+    sample = "; ".join(
+        f"h={h}: oracle h-degree pass over all {g.n} vertices ({r['pass_s']:.2f} s, {threads} threads, measured) + "
+        f"Algorithm 1 for {r['removed']} removals ({r['peel_s']:.2f} s, 1 thread, measured)"
+        + (f", extrapolated to {g.n} removals" if r["extrapolated"] else ", the whole decomposition")
+        for h, r in zip(hs, last))
+    pair, _ = oracle_config1_pair()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * len(hs) / value,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(est),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic", "config": {"workload": workload_name(args, g), "hs": hs, "n": g.n, "m": g.m},
-        "cpu_baseline": dict(last, value=value),
+        "extrapolated": extrapolated,
+        "measured_s": {str(h): {"pass_s": r["pass_s"], "peel_s": r["peel_s"], "removed": r["removed"]}
+                       for h, r in zip(hs, last)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                         "extrapolated": extrapolated},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "config1_pair": pair,
         "wall_s": wall,
     }
     print(json.dumps(line), flush=True)
@@ -398,7 +408,20 @@ def run_ours(args):
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_sample(g, hs, args.cpu_seconds, rank)
+        line["cpu_baseline"] = cpu_baseline_sample(g, hs, args.ref_removals)
+        # the measured pair on the one configuration the oracle finishes in
+        # seconds: the same decomposition on the GPU (CUDA events, warm) and
+        # by the oracle (Algorithm 1, one thread, end to end)
+        pair, core1 = oracle_config1_pair()
+        g1 = gg.config1_er()
+        with kh.KHCore.from_graph(g1, flags=kh.FLAG_TRUST_INPUT) as c1:
+            for _ in range(3):
+                c1.decompose(2)
+            runs = [kh.khcore_decompose_ex(c1.ctx, 2, want_rounds=False) for _ in range(5)]
+        pair["gpu_ms"] = statistics.median(st["device_ms"] for _, _, st in runs)
+        pair["oracle_ms"] = 1e3 * pair.pop("oracle_s")
+        pair["identical"] = bool(all(np.array_equal(c, core1) for c, _, _ in runs))
+        line["config1_pair"] = pair
     kh.khcore_destroy(ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)
