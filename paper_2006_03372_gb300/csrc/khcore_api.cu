@@ -63,6 +63,8 @@ struct khcore_ctx {
     int W_alloc = 0;
     uint64_t *V = nullptr, *F[2] = {nullptr, nullptr};
     uint8_t *flag[2] = {nullptr, nullptr};
+    uint64_t *Fx = nullptr;                    // third frontier array of the persistent kernel's ring
+    uint8_t *flagx = nullptr, *tflag = nullptr;  // its flags; vertices already in the touched list
     int32_t *Q[3] = {nullptr, nullptr, nullptr};
     int2 *I[3] = {nullptr, nullptr, nullptr};
     int32_t *T = nullptr;
@@ -263,18 +265,21 @@ khcore_status ensure_bfs(khcore_ctx *c, int W)
     cudaFree(c->V);
     cudaFree(c->F[0]);
     cudaFree(c->F[1]);
+    cudaFree(c->Fx);
     cudaFree(c->cnt);
-    c->V = c->F[0] = c->F[1] = nullptr;
+    c->V = c->F[0] = c->F[1] = c->Fx = nullptr;
     c->cnt = nullptr;
     c->W_alloc = 0;
     const size_t words = (size_t)std::max(c->n, 1) * W;
     CU(dev_alloc(&c->V, words));
     CU(dev_alloc(&c->F[0], words));
     CU(dev_alloc(&c->F[1], words));
+    CU(dev_alloc(&c->Fx, words));
     CU(dev_alloc(&c->cnt, (size_t)64 * W));
     CU(cudaMemsetAsync(c->V, 0, words * sizeof(uint64_t), c->stream));
     CU(cudaMemsetAsync(c->F[0], 0, words * sizeof(uint64_t), c->stream));
     CU(cudaMemsetAsync(c->F[1], 0, words * sizeof(uint64_t), c->stream));
+    CU(cudaMemsetAsync(c->Fx, 0, words * sizeof(uint64_t), c->stream));
     CU(cudaMemsetAsync(c->cnt, 0, (size_t)64 * W * sizeof(int32_t), c->stream));
     c->W_alloc = W;
     return KHCORE_OK;
@@ -292,8 +297,11 @@ khcore_status clear_if_dirty(khcore_ctx *c)
     CU(cudaMemsetAsync(c->V, 0, words * sizeof(uint64_t), c->stream));
     CU(cudaMemsetAsync(c->F[0], 0, words * sizeof(uint64_t), c->stream));
     CU(cudaMemsetAsync(c->F[1], 0, words * sizeof(uint64_t), c->stream));
+    CU(cudaMemsetAsync(c->Fx, 0, words * sizeof(uint64_t), c->stream));
     CU(cudaMemsetAsync(c->flag[0], 0, nflag, c->stream));
     CU(cudaMemsetAsync(c->flag[1], 0, nflag, c->stream));
+    CU(cudaMemsetAsync(c->flagx, 0, nflag, c->stream));
+    CU(cudaMemsetAsync(c->tflag, 0, nflag, c->stream));
     CU(cudaMemsetAsync(c->cnt, 0, (size_t)64 * c->W_alloc * sizeof(int32_t), c->stream));
     CU(cudaMemsetAsync(c->dcount, 0, sizeof(int32_t) * (size_t)std::max(c->n, 1), c->stream));
     CU(cudaMemsetAsync(c->wsum, 0, sizeof(int32_t) * (size_t)std::max(c->n, 1), c->stream));
@@ -341,8 +349,13 @@ khcore_status hdeg_sources(khcore_ctx *c, int W, int32_t h, const int32_t *src, 
     b.ctl = c->ctl;
     b.cnt = c->cnt;
     b.edges = c->edges;
+    b.Fx = nullptr;  // the per-phase kernels use two-slot levels
+    b.flagx = nullptr;
+    b.tflag = nullptr;
     b.rowcnt = rowcnt;
     b.row_first = 0;
+    b.row_sign = 1;
+    b.newcnt = nullptr;
     b.alg_bytes = c->alg;
     b.slev = nullptr;
     b.cum = nullptr;
@@ -453,6 +466,8 @@ khcore_status setup_ctx(khcore_ctx *c, const std::vector<int32_t> &rp, const std
     A(dev_alloc(&c->alg, 1));
     A(dev_alloc(&c->flag[0], nflag));
     A(dev_alloc(&c->flag[1], nflag));
+    A(dev_alloc(&c->flagx, nflag));
+    A(dev_alloc(&c->tflag, nflag));
     for (int k = 0; k < 3; k++) {
         A(dev_alloc(&c->Q[k], (size_t)n));
         // push items: every frontier row in chunks of at least 8 entries
@@ -510,6 +525,8 @@ khcore_status setup_ctx(khcore_ctx *c, const std::vector<int32_t> &rp, const std
         e = cudaMemcpyAsync(c->gid, gid_host->data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->flag[0], 0, nflag, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->flag[1], 0, nflag, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->flagx, 0, nflag, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->tflag, 0, nflag, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return fail(nullptr, KHCORE_ECUDA, "graph upload: %s", cudaGetErrorString(e));
     return KHCORE_OK;
@@ -823,7 +840,13 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         L.b.ctl = c->ctl;
         L.b.cnt = c->cnt;
         L.b.edges = c->edges;
+        L.b.Fx = c->Fx;
+        L.b.flagx = c->flagx;
+        L.b.tflag = c->tflag;
         L.b.rowcnt = nullptr;
+        L.b.row_first = 0;
+        L.b.row_sign = 1;
+        L.b.newcnt = nullptr;
         L.b.alg_bytes = c->alg;
         L.b.slev = nullptr;
         L.b.cum = nullptr;
@@ -1045,7 +1068,7 @@ void khcore_destroy(khcore_ctx *c)
     void *bufs[] = {c->row_ptr, c->col, c->classes, c->gid, c->kg, c->ming, c->hg, c->gcls, c->cls_off, c->nAc,
                     c->nDc, c->inner, c->clsh, c->dcls, c->dcount, c->comb, c->slack, c->wsum, c->cand, c->voff_d, c->order_d, c->bnext, c->bstats, c->mind, c->minub, c->ncand, c->cls_size, c->gs, c->pstats,
                     c->cls_src, c->alive, c->deg, c->core, c->rnd, c->src, c->vis, c->st, c->V, c->F[0], c->F[1],
-                    c->flag[0], c->flag[1], c->Q[0], c->Q[1], c->Q[2], c->I[0], c->I[1], c->I[2], c->T, c->ctl,
+                    c->Fx, c->flagx, c->tflag, c->flag[0], c->flag[1], c->Q[0], c->Q[1], c->Q[2], c->I[0], c->I[1], c->I[2], c->T, c->ctl,
                     c->cnt, c->edges, c->alg};
     for (void *p : bufs) cudaFree(p);
     for (cudaEvent_t e : c->tev) cudaEventDestroy(e);

@@ -163,6 +163,7 @@ __device__ __forceinline__ uint64_t elig_mask(const BfsBufs &b, int j, int32_t y
 struct Acc {
     unsigned long long scanned;  // plain-BFS-equivalent CSR entries
     unsigned long long fe;       // degree sum of vertices appended to the next frontier
+    unsigned long long newv;     // vertices first reached at the last level (when b.newcnt is set)
 };
 
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
@@ -302,7 +303,7 @@ __device__ __forceinline__ void dev_seed(const int32_t *src, int32_t ns, BfsBufs
         b.flag[0][s] = 1;
         b.T[i] = s;
     }
-    Acc dummy{0, 0};
+    Acc dummy{0, 0, 0};
     append_frontier<W>(i < ns, s, (int32_t)d, b, 0, dummy, rp);  // Q[0] and the level-0 push items
     const unsigned long long ws = warp_sum(d);
     if ((i & 31) == 0 && ws) atomicAdd(&s_fe, ws);
@@ -337,6 +338,7 @@ __device__ __forceinline__ void finish_vertex(bool act, int32_t y, int32_t dy, u
     const bool lead = act && gany && gi == 0;
     if (lead) fln[y] = 1;
     append_frontier<W>(lead, y, dy, b, nslot, acc, rp);
+    if (b.tflag && lead && !gv) b.tflag[y] = 1;  // first visit (fused levels keep T by tflag)
     warp_append(lead && !gv, y, b.T, &b.ctl->t);
 }
 
@@ -382,7 +384,12 @@ __device__ __forceinline__ void pull_groups(const int32_t *list, int32_t count, 
             int32_t rc = __popcll(nw & row_mask(gi, b.row_first));
 #pragma unroll
             for (int off = 1; off < G; off <<= 1) rc += __shfl_xor_sync(kFull, rc, off);
-            if (act && gi == 0 && rc) atomicAdd(&b.rowcnt[y], rc);
+            if (act && gi == 0 && rc) atomicAdd(&b.rowcnt[y], b.row_sign * rc);
+        }
+        if (LAST && b.newcnt) {  // uniform
+            const unsigned gm = (G == 32) ? kFull : ((1u << G) - 1u);
+            const unsigned nb = __ballot_sync(kFull, nw != 0), vb = __ballot_sync(kFull, v != 0);
+            if (act && gi == 0 && ((nb >> (grp * G)) & gm) && !((vb >> (grp * G)) & gm)) acc.newv++;
         }
         if (!LAST) finish_vertex<W, G>(act, y, dy, nw, v, gi, grp, V, Fn, fln, b, nslot, acc, rp);
     }
@@ -393,7 +400,46 @@ __device__ __forceinline__ void pull_groups(const int32_t *list, int32_t count, 
 // LAST: the expansion reaching distance h; only counts (pull) or counts and
 // records the rows to clear (push).
 // ---------------------------------------------------------------------------
-template <int W, bool LAST>
+// FUSED (persistent kernel): one grid phase per level instead of two (level,
+// then post). The frontier arrays and flags rotate over three slots (F[0],
+// F[1], Fx and flag[0], flag[1], flagx, indexed like the lists Q), so the
+// rows of the frontier the previous level expanded (slot (lvl+2)%3) are
+// cleared here: nothing else reads or writes that slot during this level.
+// The push direction writes the bits it discovers into V at once (atomicOr)
+// and enters first-visited vertices into T (claimed in tflag), so V and T
+// are complete at every barrier and no fold is needed. The last level writes
+// neither V nor T.
+template <class T>
+__device__ __forceinline__ T *ring3(T *a0, T *a1, T *a2, int i)
+{
+    return i == 0 ? a0 : (i == 1 ? a1 : a2);
+}
+
+// Clear the frontier rows and flags of the vertices listed in ring slot
+// `slot` (fused levels). W lanes per vertex.
+template <int W>
+__device__ __forceinline__ void clear_slot(const BfsBufs &b, int slot)
+{
+    const int lane = threadIdx.x & 31;
+    const int j = lane % W, grp = lane / W;
+    constexpr int VPW = 32 / W;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int32_t nq = b.ctl->q[slot];
+    const int32_t *Qs = pick3(b.Q, slot);
+    uint64_t *Fs = ring3(b.F[0], b.F[1], b.Fx, slot);
+    uint8_t *fls = ring3(b.flag[0], b.flag[1], b.flagx, slot);
+    for (int64_t base = warp * VPW; base < nq; base += nwarps * VPW) {
+        const int64_t idx = base + grp;
+        if (idx < nq) {
+            const int32_t x = Qs[idx];
+            Fs[(size_t)x * W + j] = 0;
+            if (j == 0) fls[x] = 0;
+        }
+    }
+}
+
+template <int W, bool LAST, bool FUSED = false>
 __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, BfsBufs b,
                                                   int lvl, BfsTuning tune)
 {
@@ -403,13 +449,14 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
 
     const int cslot = lvl % 3, nslot = (lvl + 1) % 3;
     const int cb = lvl & 1, nb_ = cb ^ 1;
-    const uint64_t *Fc = pick2(b.F, cb);
-    const uint8_t *flc = pick2(b.flag, cb);
-    uint64_t *Fn = pick2(b.F, nb_);
-    uint8_t *fln = pick2(b.flag, nb_);
+    const uint64_t *Fc = FUSED ? ring3(b.F[0], b.F[1], b.Fx, cslot) : pick2(b.F, cb);
+    const uint8_t *flc = FUSED ? ring3(b.flag[0], b.flag[1], b.flagx, cslot) : pick2(b.flag, cb);
+    uint64_t *Fn = FUSED ? ring3(b.F[0], b.F[1], b.Fx, nslot) : pick2(b.F, nb_);
+    uint8_t *fln = FUSED ? ring3(b.flag[0], b.flag[1], b.flagx, nslot) : pick2(b.flag, nb_);
     uint64_t *V = b.V;
     const bool push = use_push(b.ctl, cslot, tune);
 
+    if (FUSED && lvl > 0) clear_slot<W>(b, (lvl + 2) % 3);
     for (int i = threadIdx.x; i < 64 * W; i += blockDim.x) cnt_s[i] = 0;
     // Algorithmic bytes of this level. Pull: 4 n_b (row offsets) + 4 m_b
     // (column ids) + 16 W n_b (own visited and next-frontier rows) over the
@@ -434,7 +481,7 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
     const int32_t *col = g.col;
     Swar sw;
     sw.reset();
-    Acc acc{0, 0};
+    Acc acc{0, 0, 0};
 
     if (push) {
         // ---------------- push: frontier vertices scatter to neighbours ----
@@ -448,19 +495,23 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
         // one edge of the expansion: y = col[e] gets fx & ~V(y)
         auto edge = [&](int32_t e, int32_t e1, uint64_t fx) {
             int32_t y = -1;
-            uint64_t nbits = 0, fresh = 0;
+            uint64_t nbits = 0, fresh = 0, v = 0;
             if (e < e1) {
                 y = __ldg(&col[e]);
                 if (is_alive(alive, y)) {
-                    nbits = fx & ~V[(size_t)y * W + j];
+                    v = V[(size_t)y * W + j];
+                    nbits = fx & ~v;
                     if (nbits) {
                         const unsigned long long old =
                             atomicOr(reinterpret_cast<unsigned long long *>(&Fn[(size_t)y * W + j]),
                                      (unsigned long long)nbits);
                         fresh = nbits & ~(uint64_t)old;
+                        if (FUSED && !LAST && fresh)
+                            atomicOr(reinterpret_cast<unsigned long long *>(&V[(size_t)y * W + j]),
+                                     (unsigned long long)fresh);
                         if (b.rowcnt) {
                             const uint64_t rf = fresh & row_mask(j, b.row_first);
-                            if (rf) atomicAdd(&b.rowcnt[y], __popcll(rf));
+                            if (rf) atomicAdd(&b.rowcnt[y], b.row_sign * __popcll(rf));
                         }
                     }
                 }
@@ -474,7 +525,23 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
                 claimed = flag_claim(fln, y);
                 dy = rp[y + 1] - rp[y];
             }
-            append_frontier<W>(claimed, y, dy, b, nslot, acc, rp);
+            append_frontier<W>(claimed, y, (FUSED && LAST) ? 0 : dy, b, nslot, acc, rp);
+            if constexpr (FUSED) {
+                const unsigned vany = __ballot_sync(kFull, v != 0);
+                const bool gv = ((vany >> (grp * W)) & gmask) != 0;
+                if (!LAST) {
+                    // first visit of y in this batch: the touched list; and
+                    // the plain-BFS edges of the sources that reach it now
+                    const unsigned fany = __ballot_sync(kFull, fresh != 0);
+                    const bool gfresh = ((fany >> (grp * W)) & gmask) != 0;
+                    const bool first = (j == 0) && gfresh && flag_claim(b.tflag, y);
+                    warp_append(first, y, b.T, &b.ctl->t);
+                    const int32_t dyg = __shfl_sync(kFull, dy, lane & ~(W - 1));
+                    if (fresh) acc.scanned += (unsigned long long)__popcll(fresh) * (unsigned long long)dyg;
+                } else if (b.newcnt && claimed && !gv) {
+                    acc.newv++;
+                }
+            }
         };
         // work items: up to C entries of one frontier row each, one warp per item
         for (int64_t it = warp; it < ni; it += nwarps) {  // warp-uniform
@@ -527,7 +594,11 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
                         int32_t rc = __popcll(nw & row_mask(lane, b.row_first));
 #pragma unroll
                         for (int off = 1; off < 32; off <<= 1) rc += __shfl_xor_sync(kFull, rc, off);
-                        if (act && lane == 0 && rc) atomicAdd(&b.rowcnt[y], rc);
+                        if (act && lane == 0 && rc) atomicAdd(&b.rowcnt[y], b.row_sign * rc);
+                    }
+                    if (LAST && b.newcnt) {
+                        const unsigned nb = __ballot_sync(kFull, nw != 0), vb = __ballot_sync(kFull, v != 0);
+                        if (act && lane == 0 && nb && !vb) acc.newv++;
                     }
                     if (!LAST) finish_vertex<W, 32>(act, y, e1 - e0, nw, v, lane, 0, V, Fn, fln, b, nslot, acc, rp);
                 }
@@ -539,9 +610,11 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
     swar_flush<W>(sw, cnt_s);
     const unsigned long long sc = warp_sum(acc.scanned);
     const unsigned long long fe = warp_sum(acc.fe);
+    const unsigned long long nv = warp_sum(acc.newv);
     if (lane == 0) {
         if (sc) atomicAdd(b.edges, sc);
         if (fe) atomicAdd(&b.ctl->fe[nslot], fe);
+        if (nv) atomicAdd(b.newcnt, nv);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < 64 * W; i += blockDim.x) {
@@ -682,6 +755,57 @@ __device__ __forceinline__ void dev_end(BfsBufs b, const int32_t *src, int32_t n
 }
 
 
+// End of a batch run with fused levels: zero the V rows and tflag of T, the
+// frontier rows and flags of the last level's slot and of the slot its push
+// direction wrote, and the per-source counts. Per source position i < ns:
+// when deg is set, deg[src[i]] = its count; when p.ming is set too, the count
+// also goes into its graph's exact minimum (the refine step of the lazy
+// mode). When slack is set (the lazy mode's batch seeded at the deleted set,
+// whose row counts were already taken off deg), every alive vertex of T (the
+// vertices within h-1 of the sources) widens its slack by
+// min(extra, wsum[u]) (Observation 2: what it loses beyond the sources it
+// still reaches lies within h-1 of them), extra = |T| (those vertices plus
+// the sources), capped so that deg - slack stays >= 0; wsum is reset.
+template <int W>
+__device__ __forceinline__ void dev_end_fused(const BfsBufs &b, const int32_t *src, int32_t ns, int32_t h,
+                                              int32_t *deg, const PeelView *pmin, int32_t *slack,
+                                              const uint32_t *alive)
+{
+    const int lane = threadIdx.x & 31;
+    const int j = lane % W;
+    const int grp = lane / W;
+    constexpr int VPW = 32 / W;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t warp = tid >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int32_t nt = b.ctl->t;
+    for (int64_t base = warp * VPW; base < nt; base += nwarps * VPW) {
+        const int64_t idx = base + grp;
+        if (idx < nt) {
+            const int32_t u = b.T[idx];
+            b.V[(size_t)u * W + j] = 0;
+            if (j == 0) {
+                b.tflag[u] = 0;
+                if (slack && is_alive(alive, u)) {
+                    const int32_t d = deg[u];
+                    const int32_t ex = min(nt, b.wsum ? b.wsum[u] : nt);
+                    const long long sl = (long long)slack[u] + ex;
+                    slack[u] = (int32_t)(sl < d ? sl : d);
+                }
+                if (b.wsum) b.wsum[u] = 0;
+            }
+        }
+    }
+    clear_slot<W>(b, (h - 1) % 3);
+    clear_slot<W>(b, h % 3);
+    if (tid < ns) {
+        const int32_t c = b.cnt[tid];
+        b.cnt[tid] = 0;
+        if (deg && !slack) deg[src[tid]] = c;
+        if (pmin) atomicMin(&pmin->ming[pmin->gid ? __ldg(&pmin->gid[src[tid]]) : 0], c);
+    }
+}
+
 // ===========================================================================
 // Peel rounds
 // ===========================================================================
@@ -724,7 +848,10 @@ __device__ __forceinline__ void warp_min_by_graph(int32_t m, int32_t g, int32_t 
 }
 
 // Per-graph minimum over alive vertices: exact h-degrees into p.ming; in the
-// lazy mode, vertices with slack give their lower bound deg - slack to p.mind.
+// lazy mode, vertices with slack give their lower bound deg - slack to p.mind
+// (and their upper bound deg to p.minub). One graph: every thread keeps its
+// own minima, reduced over the block, one atomic per block and quantity.
+// Whole blocks call.
 __device__ __forceinline__ void dev_min_alive_deg(int32_t n, const uint32_t *alive,
                                                           const int32_t *deg, PeelView p)
 {
@@ -732,6 +859,57 @@ __device__ __forceinline__ void dev_min_alive_deg(int32_t n, const uint32_t *ali
     const int32_t nw = (n + 31) >> 5;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    if (p.G == 1) {
+        __shared__ int32_t red[3][32];
+        int32_t me = INT_MAX, ml = INT_MAX, mu = INT_MAX;
+        for (int64_t w = warp; w < nw; w += nwarps) {
+            const uint32_t aw = alive[w];
+            if (!aw) continue;  // warp-uniform
+            const int32_t v = (int32_t)w * 32 + lane;
+            if (v < n && ((aw >> lane) & 1u)) {
+                const int32_t d = deg[v];
+                const int32_t sl = p.slack ? p.slack[v] : 0;
+                if (sl == 0) {
+                    me = min(me, d);
+                } else {
+                    ml = min(ml, d - sl);
+                    mu = min(mu, d);
+                }
+            }
+        }
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+            me = min(me, __shfl_xor_sync(kFull, me, off));
+            ml = min(ml, __shfl_xor_sync(kFull, ml, off));
+            mu = min(mu, __shfl_xor_sync(kFull, mu, off));
+        }
+        const int wid = threadIdx.x >> 5;
+        if (lane == 0) {
+            red[0][wid] = me;
+            red[1][wid] = ml;
+            red[2][wid] = mu;
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int nwb = blockDim.x >> 5;
+            me = lane < nwb ? red[0][lane] : INT_MAX;
+            ml = lane < nwb ? red[1][lane] : INT_MAX;
+            mu = lane < nwb ? red[2][lane] : INT_MAX;
+#pragma unroll
+            for (int off = 16; off; off >>= 1) {
+                me = min(me, __shfl_xor_sync(kFull, me, off));
+                ml = min(ml, __shfl_xor_sync(kFull, ml, off));
+                mu = min(mu, __shfl_xor_sync(kFull, mu, off));
+            }
+            if (lane == 0) {
+                if (me != INT_MAX) atomicMin(&p.ming[0], me);
+                if (p.slack && ml != INT_MAX) atomicMin(&p.mind[0], ml);
+                if (p.slack && mu != INT_MAX) atomicMin(&p.minub[0], mu);
+            }
+        }
+        __syncthreads();
+        return;
+    }
     for (int64_t w = warp; w < nw; w += nwarps) {
         const int32_t v = (int32_t)w * 32 + lane;
         const uint32_t aw = alive[w];
@@ -858,7 +1036,7 @@ __device__ __forceinline__ void dev_peel_compact(int32_t n, const int32_t *rp,
     for (int64_t w = warp; w < nw; w += nwarps) {
         const uint32_t aw = alive[w];
         if (!aw) {  // warp-uniform
-            if (lane == 0) vis[w] = 0;
+            if (lane == 0 && vis) vis[w] = 0;
             continue;
         }
         const int32_t y = (int32_t)w * 32 + lane;
@@ -871,7 +1049,7 @@ __device__ __forceinline__ void dev_peel_compact(int32_t n, const int32_t *rp,
         }
         const unsigned mask = __ballot_sync(kFull, del);
         if (!mask) {  // warp-uniform
-            if (lane == 0) vis[w] = 0;
+            if (lane == 0 && vis) vis[w] = 0;
             continue;
         }
         unsigned long long dsum = 0;
@@ -885,7 +1063,7 @@ __device__ __forceinline__ void dev_peel_compact(int32_t n, const int32_t *rp,
         int32_t base = 0;
         if (lane == 0) {
             alive[w] = aw & ~mask;
-            vis[w] = mask;  // every word of vis is written: it starts the round's affected BFS
+            if (vis) vis[w] = mask;  // every word of vis is written: it starts the round's affected BFS
             base = atomicAdd(&st->aq[0], __popc(mask));
             atomicAdd(&st->nD, __popc(mask));
             atomicSub(&st->alive, __popc(mask));

@@ -75,6 +75,12 @@ struct BfsBufs {
     uint64_t *V;
     uint64_t *F[2];
     uint8_t *flag[2];
+    // Fused levels (persistent kernel) only: the third frontier array and
+    // flag array of the three-slot ring, and one byte per vertex marking the
+    // vertices already in T (all zero between batches).
+    uint64_t *Fx;
+    uint8_t *flagx;
+    uint8_t *tflag;
     int32_t *Q[3];
     int2 *I[3];
     int32_t *T;
@@ -83,6 +89,8 @@ struct BfsBufs {
     unsigned long long *edges;
     int32_t *rowcnt;
     int32_t row_first;
+    int32_t row_sign;               // +1: rowcnt[y] += count; -1: rowcnt[y] -= count
+    unsigned long long *newcnt;     // optional: += vertices first reached at the last level
     unsigned long long *alg_bytes;  // algorithmic bytes of every level run (see dev_level)
     // Optional eligibility of the column counts (the ball-restricted label BFS
     // of the paper's update, Algorithm 3): when slev is set, vertex y counts
@@ -123,6 +131,7 @@ struct PeelState {
     int32_t round;    // current round
     int32_t err;      // device-side consistency error code (0 = none)
     int32_t aq[3];    // affected-BFS frontier list lengths (ring of three)
+    int32_t lvl_set;  // persistent kernel: the level step of this round already ran
     unsigned long long m_alive;  // CSR entries of alive vertices
 };
 

@@ -96,17 +96,32 @@ struct PersistArgs {
     unsigned long long timeout_ns;
 };
 
+// What one BFS batch of the persistent kernel produces besides the column
+// counts.
+struct BatchOpt {
+    int32_t *rowcnt = nullptr;  // row counts (see BfsBufs::rowcnt), or nullptr
+    int32_t row_first = 0;
+    int32_t row_sign = 1;       // -1: the row counts are taken off rowcnt
+    bool weights = false;       // lazy mode, seeded at the deleted set: ball bounds into wsum
+    bool lazy_end = false;      // lazy mode, seeded at the deleted set: slack update of T at the end
+    bool min_fold = false;      // fold the sources' h-degrees into their graph's exact minimum
+};
+
 // One batch of the multi-source BFS (sources src[0..ns), h levels), every
-// block taking part; phases separated by barriers. Returns false on timeout.
+// block taking part, with fused levels (dev_level<W, LAST, true>): a barrier
+// to reset the level ring, one phase per level, one to finish (h + 2
+// barriers; one more before level h-2 for the h-2 ball weights when h >= 3).
+// Returns false on timeout.
 template <int W>
-__device__ bool bfs_batch(const PersistArgs &a, const int32_t *src, int32_t ns, int32_t h, int32_t *rowcnt,
-                          int32_t row_first, bool weights)
+__device__ bool bfs_batch(const PersistArgs &a, const int32_t *src, int32_t ns, int32_t h, const BatchOpt &o)
 {
     BfsBufs b = a.b;
-    b.rowcnt = rowcnt;
-    b.row_first = row_first;
-    b.wsum = weights ? a.wsum : nullptr;
+    b.rowcnt = o.rowcnt;
+    b.row_first = o.row_first;
+    b.row_sign = o.row_sign;
+    b.wsum = o.weights ? a.wsum : nullptr;
     b.wdeg = a.deg;
+    b.newcnt = o.lazy_end ? reinterpret_cast<unsigned long long *>(&a.ps->affected_total) : nullptr;
     LevelCtl *ctl = b.ctl;
     // reset the level ring and place the sources (level 0)
     if (!grid_sync(a.gs, a.timeout_ns, [&] {
@@ -132,9 +147,10 @@ __device__ bool bfs_batch(const PersistArgs &a, const int32_t *src, int32_t ns, 
                 b.V[(size_t)s * W + word] = bit;     // V rows are zero between batches
                 b.F[0][(size_t)s * W + word] = bit;  // so are F rows
                 b.flag[0][s] = 1;
+                b.tflag[s] = 1;
                 b.T[i] = s;
             }
-            Acc acc0{0, 0};
+            Acc acc0{0, 0, 0};
             append_frontier<W>(i < ns, s, (int32_t)d, b, 0, acc0, a.g.row_ptr);  // Q[0] and level-0 push items
             const unsigned long long ws = warp_sum(acc0.fe);
             if (lane == 0 && ws) {
@@ -146,47 +162,53 @@ __device__ bool bfs_batch(const PersistArgs &a, const int32_t *src, int32_t ns, 
     BfsTuning tune;
     tune.alpha = a.alpha;
     for (int lvl = 0; lvl < h; lvl++) {
-        if (!grid_sync(a.gs, a.timeout_ns, [&] { a.ps->level_steps++; })) return false;
+        // the slot this level appends to was cleared by the previous level
+        if (!grid_sync(a.gs, a.timeout_ns, [&] {
+                a.ps->level_steps++;
+                const int sl = (lvl + 1) % 3;
+                ctl->q[sl] = 0;
+                ctl->qi[sl] = 0;
+                ctl->fe[sl] = 0;
+            }))
+            return false;
         tune.m_alive = *((volatile unsigned long long *)&a.st->m_alive);
         tune.n_alive = *((volatile int32_t *)&a.st->alive);
-        if (lvl == h - 1) {
-            // the last level reads the visited rows and the touched list
-            // without changing them, so the weights of the sources within
-            // h-1 are taken in the same phase
-            if (b.wsum && h >= 2) dev_weight_pass<W>(b, src, a.g.row_ptr, a.alive, true);
-            dev_level<W, true>(a.g, a.alive, b, lvl, tune);
-        } else {
-            dev_level<W, false>(a.g, a.alive, b, lvl, tune);
-        }
-        if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return false;
-        if (lvl == h - 1)
-            dev_post<W, true>(a.g, b, lvl, tune);
-        else
-            dev_post<W, false>(a.g, b, lvl, tune);
-        if (b.wsum && lvl == h - 3) {
-            if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return false;
+        if (b.wsum && h >= 3 && lvl == h - 2) {
+            // V holds every source within h-2 now; the next level adds more
             dev_weight_pass<W>(b, src, a.g.row_ptr, a.alive, false);
+            if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return false;
+        }
+        if (lvl == h - 1) {
+            // the last level writes neither V nor T, so the weights of the
+            // sources within h-1 are taken in the same phase
+            if (b.wsum && h >= 2) dev_weight_pass<W>(b, src, a.g.row_ptr, a.alive, true);
+            dev_level<W, true, true>(a.g, a.alive, b, lvl, tune);
+        } else {
+            dev_level<W, false, true>(a.g, a.alive, b, lvl, tune);
         }
     }
-    if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return false;
-    dev_end<W>(b, src, ns, a.deg);
+    if (!grid_sync(a.gs, a.timeout_ns, [&] {
+            if (o.lazy_end) a.ps->affected_total += ctl->t - ns;  // the vertices within h-1
+        }))
+        return false;
+    dev_end_fused<W>(b, src, ns, h, a.deg, o.min_fold ? &a.p : nullptr, o.lazy_end ? a.p.slack : nullptr, a.alive);
     return true;
 }
 
-// h-degrees of src[0..ns) in batches of 64*W sources.
+// h-degrees (or row counts) of src[0..ns) in batches of 64*W sources.
 template <int W>
-__device__ bool bfs_sources(const PersistArgs &a, const int32_t *src, int32_t ns, int32_t h, int32_t *rowcnt,
-                            int32_t row_first, bool weights = false)
+__device__ bool bfs_sources(const PersistArgs &a, const int32_t *src, int32_t ns, int32_t h, BatchOpt o)
 {
     constexpr int32_t S = 64 * W;
+    const int32_t row_first = o.row_first;
     for (int32_t off = 0; off < ns; off += S) {
         const int32_t cur = ns - off < S ? ns - off : S;
-        const int32_t rf = row_first > off ? row_first - off : 0;
+        o.row_first = row_first > off ? row_first - off : 0;
         // a batch of at most 64 sources runs on one-word rows: a quarter of
         // the row traffic of W = 4 for the same result (the row arrays are
         // all zero between batches in either layout)
-        const bool ok = (W > 1 && cur <= 64) ? bfs_batch<1>(a, src + off, cur, h, rowcnt, rf, weights)
-                                             : bfs_batch<W>(a, src + off, cur, h, rowcnt, rf, weights);
+        const bool ok = (W > 1 && cur <= 64) ? bfs_batch<1>(a, src + off, cur, h, o)
+                                             : bfs_batch<W>(a, src + off, cur, h, o);
         if (!ok) return false;
         if (blockIdx.x == 0 && threadIdx.x == 0) a.ps->source_batches++;
     }
@@ -213,45 +235,91 @@ __global__ void __launch_bounds__(kBlock, (W <= 4 ? 2 : 1)) k_decompose(PersistA
     // the initial h-degrees are in deg already (computed by the per-phase
     // kernels at the widest W); the rounds follow
     const bool serial_level = a.p.G <= kSerialLevelMaxGraphs;
+    const bool lazy = a.p.slack != nullptr;
     for (bool first = true;; first = false) {
         // level of every graph: k_g <- max(k_g, min alive h-degree); the
         // barrier closing the previous round advances the round counter
         if (!grid_sync(a.gs, a.timeout_ns, [&] {
                 if (!first) a.st->round++;
+                a.st->lvl_set = 0;
             }))
             return;
         mark(4);
         dev_min_alive_deg(a.g.n, a.alive, a.deg, a.p);
-        if (a.p.slack) {
+        if (lazy) {
             // lazy mode: exact recompute of the vertices whose bounds leave
-            // their fate at the coming level open
+            // their fate at the coming level open; when there are none, the
+            // level step runs in the serial step of the barrier after the
+            // selection
             if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
             dev_refine_select(a.g.n, a.alive, a.deg, a.p, a.cand);
-            if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
+            if (!grid_sync(a.gs, a.timeout_ns, [&] {
+                    int32_t tot = 0;
+                    for (int32_t c = 0; c < a.ncls; c++) tot += a.p.ncand[c];
+                    if (tot == 0 && serial_level) {
+                        dev_set_level_serial(a.p, a.st);
+                        a.st->lvl_set = 1;
+                    }
+                }))
+                return;
             mark(0);
-            for (int32_t c = 0; c < a.ncls; c++) {
-                if (c > 0 && !grid_sync(a.gs, a.timeout_ns, Nop{})) return;
-                const int32_t nc = *((volatile int32_t *)&a.p.ncand[c]);
-                if (nc <= 0) continue;
-                const int32_t *cl = a.cand + a.cls_off[c];
-                if (!bfs_sources<W>(a, cl, nc, a.cls_h[c], nullptr, 0)) return;
-                if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
-                dev_min_over_list(cl, nc, a.deg, a.p);
-                if (blockIdx.x == 0 && threadIdx.x == 0) a.ps->recomputed_total += nc;
+            if (!*((volatile int32_t *)&a.st->lvl_set)) {
+                for (int32_t c = 0; c < a.ncls; c++) {
+                    const int32_t nc = *((volatile int32_t *)&a.p.ncand[c]);
+                    if (nc <= 0) continue;
+                    BatchOpt o;
+                    o.min_fold = true;
+                    if (!bfs_sources<W>(a, a.cand + a.cls_off[c], nc, a.cls_h[c], o)) return;
+                    if (blockIdx.x == 0 && threadIdx.x == 0) a.ps->recomputed_total += nc;
+                }
+                if (!grid_sync(a.gs, a.timeout_ns, [&] {
+                        if (serial_level) dev_set_level_serial(a.p, a.st);
+                    }))
+                    return;
             }
+            mark(1);
+        } else {
+            // few graphs: the level step runs inside the barrier
+            if (!grid_sync(a.gs, a.timeout_ns, [&] {
+                    if (serial_level) dev_set_level_serial(a.p, a.st);
+                }))
+                return;
+            mark(0);
         }
-        // few graphs: the level step runs inside the barrier
-        if (!grid_sync(a.gs, a.timeout_ns, [&] {
-                if (serial_level) dev_set_level_serial(a.p, a.st);
-            }))
-            return;
-        mark(a.p.slack ? 1 : 0);
         if (!serial_level) {
             dev_set_level(a.p, a.st);
             if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
         }
         // peel set D
-        dev_peel_compact(a.g.n, a.g.row_ptr, a.alive, a.deg, a.p, a.st, a.core, a.rnd, a.vis, a.aq[0], a.dcls);
+        dev_peel_compact(a.g.n, a.g.row_ptr, a.alive, a.deg, a.p, a.st, a.core, a.rnd, lazy ? nullptr : a.vis,
+                         a.aq[0], a.dcls);
+        if (lazy) {
+            // One BFS seeded at the deleted set of each class does what the
+            // affected-set BFS and the update did: every alive vertex it
+            // reaches loses, on the spot, the deleted vertices that reach it
+            // through survivors (row counts taken off deg); those within h-1
+            // also widen their slack at the end of the batch (reading of
+            // Observation 2: what they lose besides lies within h-1 of the
+            // deleted set).
+            if (!grid_sync(a.gs, a.timeout_ns, [&] {
+                    a.ps->rounds++;
+                    a.ps->deleted_total += a.st->nD;
+                }))
+                return;
+            mark(2);
+            if (*((volatile int32_t *)&a.st->alive) == 0) break;
+            for (int32_t c = 0; c < a.ncls; c++) {
+                const int32_t nd = *((volatile int32_t *)&a.p.nDc[c]);
+                if (nd <= 0) continue;
+                BatchOpt o;
+                o.rowcnt = a.deg;
+                o.row_sign = -1;
+                o.weights = true;
+                o.lazy_end = true;
+                if (!bfs_sources<W>(a, a.dcls + a.cls_off[c], nd, a.cls_h[c], o)) return;
+            }
+            continue;
+        }
         // affected set A: BFS from D through survivors; snapshot the per-class
         // counts before the level that reaches distance h of each class
         for (int lvl = 0; lvl < a.hmax; lvl++) {
@@ -284,16 +352,6 @@ __global__ void __launch_bounds__(kBlock, (W <= 4 ? 2 : 1)) k_decompose(PersistA
             const int32_t nd = *((volatile int32_t *)&a.p.nDc[c]);
             if (na == 0) continue;
             int32_t *Ac = a.A + a.cls_off[c];
-            if (a.p.slack) {
-                // lazy mode: row counts of the deleted set, bounds for the rest
-                if (!single && nd > 0 &&
-                    !bfs_sources<W>(a, a.dcls + a.cls_off[c], nd, a.cls_h[c], a.dcount, 0, true))
-                    return;
-                if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
-                dev_apply_lazy(Ac, ni, na, single ? nullptr : a.dcount, a.deg, a.p.slack, ni + nd, a.wsum,
-                               a.dcls + a.cls_off[c], a.g.row_ptr, a.cls_h[c]);
-                continue;
-            }
             const bool count_d = na > ni && !single;
             const int32_t total = ni + (count_d ? nd : 0);
             if (total > 0) {
@@ -302,7 +360,10 @@ __global__ void __launch_bounds__(kBlock, (W <= 4 ? 2 : 1)) k_decompose(PersistA
                 // the previous class's batch from still reading the list)
                 if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
                 dev_concat(a.comb, Ac, ni, a.dcls + a.cls_off[c], count_d ? nd : 0);
-                if (!bfs_sources<W>(a, a.comb, total, a.cls_h[c], count_d ? a.dcount : nullptr, ni)) return;
+                BatchOpt o;
+                o.rowcnt = count_d ? a.dcount : nullptr;
+                o.row_first = ni;
+                if (!bfs_sources<W>(a, a.comb, total, a.cls_h[c], o)) return;
             }
             if (blockIdx.x == 0 && threadIdx.x == 0) a.ps->recomputed_total += ni;
             if (na > ni) {

@@ -245,8 +245,13 @@ extern "C" khcore_status khcore_hdegrees_static(int32_t n, int64_t m, const int3
     b.ctl = &hd->ctl;
     b.cnt = (int32_t *)(base + L.cnt);
     b.edges = &hd->edges;
+    b.Fx = nullptr;
+    b.flagx = nullptr;
+    b.tflag = nullptr;
     b.rowcnt = nullptr;
     b.row_first = 0;
+    b.row_sign = 1;
+    b.newcnt = nullptr;
     b.alg_bytes = &hd->alg_bytes;
     b.slev = nullptr;
     b.cum = nullptr;
