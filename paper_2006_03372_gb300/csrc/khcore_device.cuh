@@ -862,18 +862,29 @@ __device__ __forceinline__ void dev_min_alive_deg(int32_t n, const uint32_t *ali
     if (p.G == 1) {
         __shared__ int32_t red[3][32];
         int32_t me = INT_MAX, ml = INT_MAX, mu = INT_MAX;
-        for (int64_t w = warp; w < nw; w += nwarps) {
-            const uint32_t aw = alive[w];
-            if (!aw) continue;  // warp-uniform
-            const int32_t v = (int32_t)w * 32 + lane;
-            if (v < n && ((aw >> lane) & 1u)) {
-                const int32_t d = deg[v];
-                const int32_t sl = p.slack ? p.slack[v] : 0;
-                if (sl == 0) {
-                    me = min(me, d);
+        // U words per warp step, their loads issued together (the scan is
+        // latency-bound: a handful of words per warp)
+        constexpr int U = 4;
+        for (int64_t w0 = warp * U; w0 < nw; w0 += nwarps * U) {
+            uint32_t aw[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) aw[u] = (w0 + u < nw) ? alive[w0 + u] : 0u;
+            int32_t d[U], sl[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int32_t v = (int32_t)(w0 + u) * 32 + lane;
+                const bool a = ((aw[u] >> lane) & 1u) && v < n;
+                d[u] = a ? deg[v] : INT_MAX;
+                sl[u] = (a && p.slack) ? p.slack[v] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                if (d[u] == INT_MAX) continue;
+                if (sl[u] == 0) {
+                    me = min(me, d[u]);
                 } else {
-                    ml = min(ml, d - sl);
-                    mu = min(mu, d);
+                    ml = min(ml, d[u] - sl[u]);
+                    mu = min(mu, d[u]);
                 }
             }
         }
@@ -939,6 +950,35 @@ __device__ __forceinline__ void dev_refine_select(int32_t n, const uint32_t *ali
     const int32_t nw = (n + 31) >> 5;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    if (p.G == 1) {
+        // one graph: the threshold is one number, and no vertex is picked at
+        // all unless the least lower bound reaches it
+        const int32_t T = max(p.kg[0], min(p.ming[0], p.minub[0]));
+        if (p.mind[0] > T) return;
+        int32_t *cand0 = cand + __ldg(&p.cls_off[0]);
+        constexpr int U = 4;
+        for (int64_t w0 = warp * U; w0 < nw; w0 += nwarps * U) {
+            uint32_t aw[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) aw[u] = (w0 + u < nw) ? alive[w0 + u] : 0u;
+            int32_t d[U], sl[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int32_t v = (int32_t)(w0 + u) * 32 + lane;
+                const bool a = ((aw[u] >> lane) & 1u) && v < n;
+                sl[u] = a ? p.slack[v] : 0;
+                d[u] = a ? deg[v] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int32_t v = (int32_t)(w0 + u) * 32 + lane;
+                const bool pick = sl[u] > 0 && d[u] - sl[u] <= T;
+                if (pick) p.slack[v] = 0;
+                warp_append(pick, v, cand0, &p.ncand[0]);
+            }
+        }
+        return;
+    }
     for (int64_t w = warp; w < nw; w += nwarps) {
         const uint32_t aw = alive[w];
         if (!aw) continue;  // warp-uniform
@@ -1033,25 +1073,8 @@ __device__ __forceinline__ void dev_peel_compact(int32_t n, const int32_t *rp,
     const int32_t r = st->round;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t w = warp; w < nw; w += nwarps) {
-        const uint32_t aw = alive[w];
-        if (!aw) {  // warp-uniform
-            if (lane == 0 && vis) vis[w] = 0;
-            continue;
-        }
-        const int32_t y = (int32_t)w * 32 + lane;
-        bool del = false;
-        int32_t k = 0, gy = 0;
-        if (y < n && ((aw >> lane) & 1u)) {
-            gy = graph_of(p, y);
-            k = p.kg[gy];
-            del = deg[y] <= k;
-        }
-        const unsigned mask = __ballot_sync(kFull, del);
-        if (!mask) {  // warp-uniform
-            if (lane == 0 && vis) vis[w] = 0;
-            continue;
-        }
+    // one word of the alive bitset whose deleted lanes are `del` (mask != 0)
+    auto peel_word = [&](int64_t w, uint32_t aw, unsigned mask, bool del, int32_t y, int32_t k, int32_t gy) {
         unsigned long long dsum = 0;
         if (del) {
             core[y] = k;
@@ -1079,6 +1102,50 @@ __device__ __forceinline__ void dev_peel_compact(int32_t n, const int32_t *rp,
         } else if (del) {
             dcls[__ldg(&p.cls_off[cy]) + atomicAdd(&p.nDc[cy], 1)] = y;
         }
+    };
+    if (p.G == 1 && !vis) {
+        // one graph, no affected-set bits to write: U words per warp step,
+        // their loads issued together; only words that lose a vertex go on
+        const int32_t k = p.kg[0];
+        constexpr int U = 4;
+        for (int64_t w0 = warp * U; w0 < nw; w0 += nwarps * U) {
+            uint32_t aw[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) aw[u] = (w0 + u < nw) ? alive[w0 + u] : 0u;
+            bool del[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int32_t y = (int32_t)(w0 + u) * 32 + lane;
+                del[u] = ((aw[u] >> lane) & 1u) && y < n && deg[y] <= k;
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const unsigned mask = __ballot_sync(kFull, del[u]);
+                if (mask) peel_word(w0 + u, aw[u], mask, del[u], (int32_t)(w0 + u) * 32 + lane, k, 0);
+            }
+        }
+        return;
+    }
+    for (int64_t w = warp; w < nw; w += nwarps) {
+        const uint32_t aw = alive[w];
+        if (!aw) {  // warp-uniform
+            if (lane == 0 && vis) vis[w] = 0;
+            continue;
+        }
+        const int32_t y = (int32_t)w * 32 + lane;
+        bool del = false;
+        int32_t k = 0, gy = 0;
+        if (y < n && ((aw >> lane) & 1u)) {
+            gy = graph_of(p, y);
+            k = p.kg[gy];
+            del = deg[y] <= k;
+        }
+        const unsigned mask = __ballot_sync(kFull, del);
+        if (!mask) {  // warp-uniform
+            if (lane == 0 && vis) vis[w] = 0;
+            continue;
+        }
+        peel_word(w, aw, mask, del, y, k, gy);
     }
 }
 

@@ -49,9 +49,13 @@ struct LevelCtl {
 };
 
 // Push work items: a frontier vertex's CSR row is cut into chunks of
-// push_chunk(W) = 4 * (32/W) entries (four warp steps), so that a hub's
-// edges spread over many warps. Item = (vertex, first entry).
-__host__ __device__ constexpr int push_chunk(int W) { return 4 * (32 / W); }
+// push_chunk(W) = max(32/W, 8) entries (one warp step of 32/W edges, at
+// least 8), so that a hub's edges spread over many warps and a small
+// frontier keeps many warps busy with one short dependent chain each (load
+// the neighbour, test it, claim its bits) instead of few warps walking long
+// chunks. Item = (vertex, first entry); a frontier of total degree D makes at
+// most |frontier| + D / 8 items.
+__host__ __device__ constexpr int push_chunk(int W) { return (32 / W) > 8 ? 32 / W : 8; }
 
 // Multi-source BFS state for one batch of 64*W sources. Vertex-major: the W
 // words of vertex y are V[y*W .. y*W+W-1]; bit b of word j is source 64*j+b
