@@ -299,6 +299,48 @@ khcore_status khcore_set_push_alpha(khcore_ctx *ctx, int32_t alpha);
 khcore_status khcore_set_lazy(khcore_ctx *ctx, int32_t on);
 
 /*
+ * khcore_set_update — how the h-degrees are brought up to date after a
+ * round's deletions (one-graph contexts, and each larger graph of a batch).
+ *   0 (default)  multi-source BFS: the vertices near the deleted set are
+ *                bounded (khcore_set_lazy) or recomputed, the outer shell
+ *                counted (Observation 1 and 2, Sec. IV-A)
+ *   1            the paper's exact update (Sec. IV-A, Algorithm 3 with the
+ *                bitmaps of Sec. IV-B, Algorithm 4; driven as in Algorithm 2):
+ *                each deleted vertex's ball N_v^h is updated by the Reach DP
+ *                on the subgraph it induces, deleted vertices with pairwise
+ *                disjoint balls at once, one thread block each (see
+ *                khcore_bitmap_update). A round whose deleted set holds more
+ *                than 64 vertices, or a ball over the limits of
+ *                khcore_bitmap_update, falls back to the BFS recompute.
+ *                Rounds are driven from the host; khcore_set_lazy does not
+ *                apply.
+ * Results (core indices, rounds) are identical. EINVAL for other values.
+ */
+khcore_status khcore_set_update(khcore_ctx *ctx, int32_t mode);
+
+/*
+ * khcore_bitmap_update — the paper's exact h-degree update after deleting one
+ * vertex (Sec. IV-A, Observation 2, Theorem 1 and Algorithm 3, with the
+ * bitmaps of Sec. IV-B, Algorithm 4), on the context's graph restricted to
+ * the alive vertices.
+ *   h          hop bound, h >= 1; h > n-1 acts as n-1; at most 255
+ *   alive_in   uint8[n] (host or device): 1 = vertex present in G[alive]
+ *   v          the vertex deleted; it must be alive
+ *   deg_inout  int32[n] (host or device): in, the h-degrees in G[alive]; out,
+ *              those of the members of N_v^h updated to G[alive] - v (every
+ *              other entry unchanged)
+ *   ball_out   int64* or NULL: |N_v^h| in G[alive]
+ * Members are labelled in BFS order from v, so the members closer than h take
+ * the first bitmap bits (Table 1 labels N_v^{h-1} first). Limits: a ball of
+ * at most 65,536 members and |N_v^{h-1}| <= 256 (four 64-bit words per
+ * member); over them the call returns KHCORE_EINVAL and changes nothing. The
+ * context's own decomposition state is overwritten (a later decomposition
+ * starts afresh).
+ */
+khcore_status khcore_bitmap_update(khcore_ctx *ctx, int32_t h, const uint8_t *alive_in, int32_t v, int32_t *deg_inout,
+                                   int64_t *ball_out);
+
+/*
  * khcore_set_round_loop — how the peel rounds are driven.
  *   0 (default)  the whole decomposition runs as one cooperative persistent
  *                kernel; phases are separated by grid barriers and every

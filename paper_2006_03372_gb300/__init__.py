@@ -32,6 +32,7 @@ __all__ = [
     "khcore_status_string", "Stats",
     "KHCore", "library_path", "load_library", "khcore_batch_create", "khcore_batch_decompose", "pack_graphs",
     "khcore_hdegrees_of", "khcore_hdegrees_ex", "khcore_hdegrees_static", "Server", "request_bytes",
+    "khcore_set_update", "khcore_bitmap_update",
 ]
 
 STATUS = {0: "KHCORE_OK", 1: "KHCORE_EINVAL", 2: "KHCORE_ENOMEM", 3: "KHCORE_ECUDA",
@@ -108,6 +109,10 @@ def load_library(build_if_missing: bool = False):
         lib.khcore_set_lazy.restype = ctypes.c_int
         lib.khcore_set_graph_blocks.argtypes = [P, i32]
         lib.khcore_set_graph_blocks.restype = ctypes.c_int
+        lib.khcore_set_update.argtypes = [P, i32]
+        lib.khcore_set_update.restype = ctypes.c_int
+        lib.khcore_bitmap_update.argtypes = [P, i32, P, i32, P, ctypes.POINTER(i64)]
+        lib.khcore_bitmap_update.restype = ctypes.c_int
         lib.khcore_set_round_loop.argtypes = [P, i32]
         lib.khcore_set_round_loop.restype = ctypes.c_int
         lib.khcore_set_wait_limit.argtypes = [P, ctypes.c_uint64]
@@ -164,8 +169,9 @@ def _ptr(a, dtype=np.int32):
         return None, None
     if _is_torch(a):
         import torch
-        if a.dtype != torch.int32:
-            raise TypeError("expected an int32 tensor")
+        want = torch.uint8 if dtype == np.uint8 else torch.int32
+        if a.dtype != want:
+            raise TypeError(f"expected a {want} tensor")
         if not a.is_contiguous():
             raise ValueError("expected a contiguous tensor")
         return ctypes.c_void_p(a.data_ptr() if a.numel() else 0), a
@@ -239,6 +245,27 @@ def khcore_set_graph_blocks(ctx, mode: int) -> None:
     """0: automatic; 1: one thread block per whole graph; -1: grid-wide rounds only."""
     lib = load_library()
     _check(lib, ctx, lib.khcore_set_graph_blocks(ctx, int(mode)))
+
+
+def khcore_set_update(ctx, mode: int) -> None:
+    """0: BFS recompute (default); 1: the paper's per-deletion update (Algorithms 3/4)."""
+    lib = load_library()
+    _check(lib, ctx, lib.khcore_set_update(ctx, int(mode)))
+
+
+def khcore_bitmap_update(ctx, h: int, alive, v: int, deg):
+    """The paper's update after deleting v from G[alive] (Algorithm 3 with
+    Algorithm 4's bitmaps): returns (updated h-degrees, |N_v^h|). alive:
+    uint8[n]; deg: int32[n] h-degrees in G[alive] (not modified; a copy is
+    returned unless deg is a device tensor, which is updated in place)."""
+    lib = load_library()
+    a = np.ascontiguousarray(alive, dtype=np.uint8) if not _is_torch(alive) else alive
+    d = deg if _is_torch(deg) else np.array(deg, dtype=np.int32, copy=True)
+    pa, _ = _ptr(a, np.uint8)
+    pd, _ = _ptr(d)
+    ball = ctypes.c_int64(0)
+    _check(lib, ctx, lib.khcore_bitmap_update(ctx, int(h), pa, int(v), pd, ctypes.byref(ball)))
+    return d, int(ball.value)
 
 
 def khcore_set_round_loop(ctx, mode: int) -> None:
@@ -460,9 +487,11 @@ class KHCore:
     """Context manager around one device-resident graph."""
 
     def __init__(self, n, row_ptr, col, flags: int = 0, stream=None, words: int = 0, alpha=None, loop=None,
-                 lazy=None, blocks=None):
+                 lazy=None, blocks=None, update=None):
         self.ctx = khcore_create(n, row_ptr, col, flags, stream)
         self.n = int(n)
+        if update is not None:
+            khcore_set_update(self.ctx, update)
         if lazy is not None:
             khcore_set_lazy(self.ctx, lazy)
         if blocks is not None:

@@ -84,6 +84,9 @@ struct khcore_ctx {
     int32_t *cls_size = nullptr;          // [G] initial class sizes (device)
     GridSync *gs = nullptr;
     PersistStats *pstats = nullptr;
+    int32_t update_mode = 0;              // 0: BFS recompute; 1: the paper's per-deletion update (Algorithms 3/4)
+    UpdBufs upd{};                        // its slots, allocated on first use
+    bool upd_ready = false;
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_init = nullptr;
 
@@ -573,6 +576,83 @@ khcore_status finish_decompose(khcore_ctx *c, int32_t G, int32_t *core_out, int3
     return KHCORE_OK;
 }
 
+// Slots of the paper's per-deletion update: kUpdSlots deleted vertices per
+// wave, balls of at most kUpdCap members (and the graph's n), bitmaps of
+// kUpdWords words (|N_v^{h-1}| <= 256).
+constexpr int32_t kUpdSlots = 64;
+constexpr int32_t kUpdCap = 1 << 16;
+constexpr int32_t kUpdWords = 4;
+constexpr int32_t kUpdMaxH = 255;  // distances are stored in one byte
+
+khcore_status ensure_upd(khcore_ctx *c)
+{
+    if (c->upd_ready) return KHCORE_OK;
+    UpdBufs &u = c->upd;
+    const size_t n = (size_t)std::max(c->n, 1);
+    u.nblk = kUpdSlots;
+    u.cap = (int32_t)std::min<size_t>(kUpdCap, n);
+    u.wc = kUpdWords;
+    u.vis_words = (int64_t)((n + 31) / 32);
+    CU(dev_alloc(&u.vis, (size_t)u.nblk * (size_t)u.vis_words));
+    CU(dev_alloc(&u.list, (size_t)u.nblk * u.cap));
+    CU(dev_alloc(&u.dist, (size_t)u.nblk * u.cap));
+    CU(dev_alloc(&u.reach, (size_t)u.nblk * 2 * u.cap * u.wc));
+    CU(dev_alloc(&u.meta, (size_t)u.nblk * 4));
+    CU(dev_alloc(&u.owner, n));
+    CU(dev_alloc(&u.lab, n));
+    CU(dev_alloc(&u.done, (size_t)u.nblk));
+    CU(dev_alloc(&u.flag, 2));
+    CU(dev_alloc(&u.cand[0], n));
+    CU(dev_alloc(&u.cand[1], n));
+    CU(cudaMemsetAsync(u.vis, 0, sizeof(uint32_t) * (size_t)u.nblk * (size_t)u.vis_words, c->stream));
+    CU(launch_fill_i32(u.owner, INT_MAX, (int64_t)n, c->stream));
+    c->upd_ready = true;
+    return KHCORE_OK;
+}
+
+// The deleted vertices cand[0..nd) of G[c->alive], all still alive, updated
+// one after the other by the paper's exact update (waves of pairwise
+// disjoint closed balls) and deleted. st (nullable) gets the alive counts.
+// *fit = false (nothing changed) when some ball is over the slots' limits or
+// nd exceeds the slots of one wave; the caller then uses the BFS recompute.
+khcore_status update_deleted(khcore_ctx *c, int32_t h, int32_t nd, PeelState *st, bool *fit, int64_t *launches)
+{
+    *fit = false;
+    if (h > kUpdMaxH || nd > kUpdSlots) return KHCORE_OK;
+    khcore_status s;
+    if ((s = ensure_upd(c)) != KHCORE_OK) return s;
+    UpdBufs &u = c->upd;
+    const GraphView g = c->view();
+    int cur = 0;
+    int32_t nrem = nd, hflag[2] = {0, 0};
+    for (int wave = 0; nrem > 0; wave++) {
+        const int32_t ncur = std::min(nrem, u.nblk);
+        if (wave == 0) CU(cudaMemsetAsync(u.flag, 0, sizeof(int32_t) * 2, c->stream));
+        CU(launch_ball_claim(g, c->alive, u, u.cand[cur], ncur, h, c->stream));
+        if (wave == 0) {
+            // every ball is as large as it will get in this round: check once
+            CU(cudaMemcpyAsync(hflag, u.flag, sizeof hflag, cudaMemcpyDeviceToHost, c->stream));
+            CU(cudaStreamSynchronize(c->stream));
+            if (hflag[0]) {
+                CU(launch_ball_reset(u, u.cand[cur], ncur, c->stream));
+                if (launches) *launches += 2;
+                return KHCORE_OK;
+            }
+        }
+        CU(launch_ball_apply(g, c->alive, u, u.cand[cur], ncur, h, c->deg, st, c->stream));
+        CU(launch_ball_reset(u, u.cand[cur], ncur, c->stream));
+        CU(launch_wave_next(u, u.cand[cur], nrem, ncur, u.cand[cur ^ 1], c->stream));
+        CU(cudaMemcpyAsync(hflag, u.flag, sizeof hflag, cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        if (launches) *launches += 4;
+        if (hflag[1] >= nrem) return fail(c, KHCORE_EINTERNAL, "update wave made no progress (%d left)", nrem);
+        nrem = hflag[1];
+        cur ^= 1;
+    }
+    *fit = true;
+    return KHCORE_OK;
+}
+
 khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t *core_out, int32_t *round_out,
                         khcore_stats *stats);
 
@@ -603,6 +683,7 @@ khcore_status decompose_alone(khcore_ctx *c, int32_t gi, int32_t h, khcore_stats
     sub->Wr_req = c->Wr_req;
     sub->push_alpha = c->push_alpha;
     sub->lazy = c->lazy;
+    sub->update_mode = c->update_mode;
     sub->round_loop = c->round_loop;
     sub->wait_limit_ns = c->wait_limit_ns;
     s = decompose(sub, std::vector<int32_t>{h}, c->core + v0, c->rnd + v0, sst);
@@ -679,10 +760,14 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
     pv.cls_off = c->cls_off;
     pv.nAc = c->nAc;
     pv.nDc = c->nDc;
-    pv.slack = c->lazy ? c->slack : nullptr;
-    pv.mind = c->lazy ? c->mind : nullptr;
-    pv.minub = c->lazy ? c->minub : nullptr;
-    pv.ncand = c->lazy ? c->ncand : nullptr;
+    // the paper's per-deletion update (one graph): exact h-degrees after every
+    // round (no bounds), host-driven rounds
+    const bool paper_update = c->update_mode == 1 && G == 1 && !(c->graph_blocks > 0);
+    const bool lazy = c->lazy && !paper_update;
+    pv.slack = lazy ? c->slack : nullptr;
+    pv.mind = lazy ? c->mind : nullptr;
+    pv.minub = lazy ? c->minub : nullptr;
+    pv.ncand = lazy ? c->ncand : nullptr;
 
     CU(cudaEventRecord(c->ev0, c->stream));
     PeelState init;
@@ -815,7 +900,7 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
     CU(cudaMemcpyAsync(&init_alg, c->alg, sizeof init_alg, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     stt.level_bytes = (double)init_alg;  // the initial pass
-    const int pgrid = c->round_loop == 0 ? c->sm_count * max_blocks_per_sm_persist(Wr) : 0;
+    const int pgrid = (c->round_loop == 0 && !paper_update) ? c->sm_count * max_blocks_per_sm_persist(Wr) : 0;
     if (pgrid > 0) {
         // the whole decomposition in one cooperative launch
         PersistLaunch L;
@@ -854,7 +939,7 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         L.b.boff = 0;
         L.b.wsum = nullptr;
         L.b.wdeg = c->deg;
-        L.wsum = c->lazy ? c->wsum : nullptr;
+        L.wsum = lazy ? c->wsum : nullptr;
         L.vis = c->vis;
         L.A = c->src;
         L.dcls = c->dcls;
@@ -905,7 +990,7 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         // one round: levels, peel sets D, affected sets A, recompute deg[A];
         // the affected-BFS frontier lists reuse the BFS frontier lists Q[0..2]
         CU(launch_min_alive_deg(g, c->alive, c->deg, pv, grid, c->stream));
-        if (c->lazy) {
+        if (lazy) {
             // exact recompute of the vertices whose bounds leave their fate open
             CU(launch_refine_select(g, c->alive, c->deg, pv, c->cand, grid, c->stream));
             CU(cudaMemcpyAsync(c->nAc_host + 3 * G, c->ncand, sizeof(int32_t) * ncls, cudaMemcpyDeviceToHost,
@@ -924,6 +1009,42 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
             }
         }
         CU(launch_set_level(pv, c->st, c->stream));
+        if (paper_update) {
+            // D marked (core, round) but kept alive; then deleted one after
+            // the other by the paper's update, unless a ball is over the
+            // slots' limits (then the BFS recompute below handles the round)
+            CU(launch_peel_mark(c->n, c->alive, c->deg, c->kg, c->st, c->core, c->rnd, c->upd_ready ? c->upd.cand[0]
+                                                                                                     : c->comb,
+                                grid, c->stream));
+            CU(cudaMemcpyAsync(c->st_host, c->st, sizeof(PeelState), cudaMemcpyDeviceToHost, c->stream));
+            CU(cudaStreamSynchronize(c->stream));
+            stt.kernel_launches += 3;
+            const int32_t nd = c->st_host->nD;
+            if (nd <= 0) return fail(c, KHCORE_EINTERNAL, "round %d deleted no vertex", round);
+            bool fit = false;
+            if (c->upd_ready) {
+                if ((s = update_deleted(c, hg[0], nd, c->st, &fit, &stt.kernel_launches)) != KHCORE_OK) return s;
+            } else if (nd <= kUpdSlots && hg[0] <= kUpdMaxH) {
+                // first use: allocate the slots, then list D again into them
+                if ((s = ensure_upd(c)) != KHCORE_OK) return s;
+                CU(cudaMemcpyAsync(c->upd.cand[0], c->comb, sizeof(int32_t) * nd, cudaMemcpyDeviceToDevice,
+                                   c->stream));
+                if ((s = update_deleted(c, hg[0], nd, c->st, &fit, &stt.kernel_launches)) != KHCORE_OK) return s;
+            }
+            if (fit) {
+                CU(cudaMemcpyAsync(c->st_host, c->st, sizeof(PeelState), cudaMemcpyDeviceToHost, c->stream));
+                CU(cudaStreamSynchronize(c->stream));
+                stt.deleted_total += nd;
+                round++;
+                if (c->st_host->alive == 0) break;
+                c->st_host->round = round;
+                CU(cudaMemcpyAsync(&c->st->round, &c->st_host->round, sizeof(int32_t), cudaMemcpyHostToDevice,
+                                   c->stream));
+                continue;
+            }
+            // over the limits: the compaction below selects the same D
+            CU(cudaMemsetAsync(&c->st->nD, 0, sizeof(int32_t), c->stream));
+        }
         CU(launch_peel_compact(g, c->alive, c->deg, pv, c->st, c->core, c->rnd, c->vis, c->Q[0], c->dcls, grid,
                                c->stream));
         stt.kernel_launches += 3;
@@ -965,7 +1086,7 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
             const int32_t nd = c->nAc_host[2 * G + k];
             if (na == 0) continue;
             const bool single = (ps.nD == 1);  // every affected vertex loses exactly that one
-            if (c->lazy) {
+            if (lazy) {
                 // row counts of the deleted set; bounds for the inner vertices
                 if (!single && (s = hdeg_sources(c, Wr, cls_h[k], c->dcls + cls_off[k], nd, ps.alive,
                                                  (int64_t)ps.m_alive, &stt, c->dcount, 0, c->wsum)) != KHCORE_OK)
@@ -1071,6 +1192,9 @@ void khcore_destroy(khcore_ctx *c)
                     c->Fx, c->flagx, c->tflag, c->flag[0], c->flag[1], c->Q[0], c->Q[1], c->Q[2], c->I[0], c->I[1], c->I[2], c->T, c->ctl,
                     c->cnt, c->edges, c->alg};
     for (void *p : bufs) cudaFree(p);
+    void *ubufs[] = {c->upd.vis, c->upd.list, c->upd.dist, c->upd.reach, c->upd.meta, c->upd.owner, c->upd.lab,
+                     c->upd.done, c->upd.flag, c->upd.cand[0], c->upd.cand[1]};
+    for (void *p : ubufs) cudaFree(p);
     for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
     if (c->st_host) cudaFreeHost(c->st_host);
     if (c->nAc_host) cudaFreeHost(c->nAc_host);
@@ -1187,6 +1311,54 @@ khcore_status khcore_set_lazy(khcore_ctx *c, int32_t on)
 {
     if (!c) return KHCORE_EINVAL;
     c->lazy = on != 0;
+    return KHCORE_OK;
+}
+
+khcore_status khcore_set_update(khcore_ctx *c, int32_t mode)
+{
+    if (!c || (mode != 0 && mode != 1)) return KHCORE_EINVAL;
+    c->update_mode = mode;
+    return KHCORE_OK;
+}
+
+khcore_status khcore_bitmap_update(khcore_ctx *c, int32_t h, const uint8_t *alive_in, int32_t v, int32_t *deg_inout,
+                                   int64_t *ball_out)
+{
+    khcore_status s;
+    if ((s = check_ctx(c)) != KHCORE_OK) return s;
+    if (c->G != 1) return fail(c, KHCORE_EINVAL, "khcore_bitmap_update takes a one-graph context");
+    if (h < 1) return fail(c, KHCORE_EINVAL, "h must be >= 1 (got %d)", h);
+    if (v < 0 || v >= c->n) return fail(c, KHCORE_EINVAL, "vertex %d outside [0, %d)", v, c->n);
+    if (!alive_in || !deg_inout) return fail(c, KHCORE_EINVAL, "alive and deg must not be NULL");
+    const int32_t he = effective_h(c->n, h);
+    if (he > kUpdMaxH) return fail(c, KHCORE_EINVAL, "h = %d above the update's limit %d", he, kUpdMaxH);
+    std::vector<uint8_t> al;
+    CU(fetch(al, alive_in, (size_t)c->n));
+    if (!al[v]) return fail(c, KHCORE_EINVAL, "vertex %d is not alive", v);
+    if ((s = ensure_upd(c)) != KHCORE_OK) return s;
+    uint8_t *bytes = nullptr;
+    CU(dev_alloc(&bytes, (size_t)c->n));
+    cudaError_t e = cudaMemcpyAsync(bytes, al.data(), (size_t)c->n, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_alive_from_bytes(c->alive, bytes, c->n, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->deg, deg_inout, sizeof(int32_t) * (size_t)c->n,
+                            is_device_ptr(deg_inout) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->upd.cand[0], &v, sizeof v, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(bytes);
+    CU(e);
+    bool fit = false;
+    if ((s = update_deleted(c, he, 1, nullptr, &fit, nullptr)) != KHCORE_OK) return s;
+    if (!fit)
+        return fail(c, KHCORE_EINVAL,
+                    "the ball of vertex %d is over the update's limits (%d members, %d bitmap words per member)", v,
+                    c->upd.cap, c->upd.wc);
+    int32_t meta[4];
+    CU(cudaMemcpyAsync(meta, c->upd.meta, sizeof meta, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(deg_inout, c->deg, sizeof(int32_t) * (size_t)c->n,
+                       is_device_ptr(deg_inout) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (ball_out) *ball_out = meta[0];
     return KHCORE_OK;
 }
 

@@ -218,6 +218,37 @@ cudaError_t launch_snapshot_inner(const PeelView &p, const int32_t *cls_h, int l
 
 int max_blocks_per_sm_bfs(int W);
 
+// ---- the paper's exact update after one deletion (khcore_update.cu) ---------
+// Slots of the per-deleted-vertex update (Algorithm 3 with Algorithm 4's
+// bitmaps): one slot per thread block of a wave, each holding one ball.
+struct UpdBufs {
+    int32_t nblk;        // slots (deleted vertices per wave at most)
+    int32_t cap;         // ball members per slot
+    int32_t wc;          // 64-bit bitmap words per member: |N_v^{h-1}| <= 64 * wc (wc <= 4)
+    int64_t vis_words;   // 32-bit words of one slot's visited bitmap ((n + 31) / 32)
+    uint32_t *vis;       // [nblk * vis_words], zero between waves
+    int32_t *list;       // [nblk * cap] ball members in BFS order
+    uint8_t *dist;       // [nblk * cap] their distance from the slot's vertex
+    uint64_t *reach;     // [nblk * 2 * cap * wc] the two Reach buffers
+    int32_t *meta;       // [nblk * 4] size (-1: over the limits), d, entries listed
+    int32_t *owner;      // [n] claiming slot, INT_MAX between waves
+    int32_t *lab;        // [n] member label (valid where owner is the reader's slot)
+    int32_t *done;       // [nblk] the slot's vertex was updated and deleted
+    int32_t *flag;       // [2] any slot over the limits; candidates left after a wave
+    int32_t *cand[2];    // [n] candidate lists (current, next)
+};
+cudaError_t launch_ball_claim(const GraphView &g, const uint32_t *alive, const UpdBufs &u, const int32_t *cand,
+                              int32_t ncur, int32_t h, cudaStream_t s);
+cudaError_t launch_ball_apply(const GraphView &g, uint32_t *alive, const UpdBufs &u, const int32_t *cand,
+                              int32_t ncur, int32_t h, int32_t *deg, PeelState *st, cudaStream_t s);
+cudaError_t launch_ball_reset(const UpdBufs &u, const int32_t *cand, int32_t ncur, cudaStream_t s);
+cudaError_t launch_wave_next(const UpdBufs &u, const int32_t *cand, int32_t nrem, int32_t ncur, int32_t *out,
+                             cudaStream_t s);
+cudaError_t launch_peel_mark(int32_t n, const uint32_t *alive, const int32_t *deg, const int32_t *kg, PeelState *st,
+                             int32_t *core, int32_t *rnd, int32_t *cand, int grid, cudaStream_t s);
+cudaError_t launch_alive_from_bytes(uint32_t *alive, const uint8_t *bytes, int32_t n, cudaStream_t s);
+cudaError_t launch_fill_i32(int32_t *p, int32_t val, int64_t count, cudaStream_t s);
+
 // ---- persistent decomposition (khcore_persist.cu) ---------------------------
 
 // Grid barrier state (zero before the launch); err = 1 after a timed-out wait.
