@@ -443,9 +443,11 @@ int orc_peel_bitmap(int32_t n, const int32_t *row_ptr, const int32_t *col, int32
 /*   cnt = [v in S] + |{sampled u_j, dist(v, u_j) <= h - s, not reached}|    */
 /*   from select[u] (<= as in Algorithm 4, so that S = V gives Algorithm 2   */
 /*   exactly).                                                               */
-/*   A vertex whose initial ball holds no sampled vertex (select0 = 0, d0 >  */
-/*   0) has no rate; its estimate drops by 1 for every deleted vertex within */
-/*   h of it.                                                                */
+/*   A vertex whose initial ball holds no sampled vertex (select0 = 0) has  */
+/*   no rate (Algorithm 5 divides by it): it keeps its exact h-degree,       */
+/*   recomputed by BFS after every deletion within h of it (the estimate    */
+/*   every full sample gives; it makes each estimate a function of the      */
+/*   surviving vertex set, like select and the h-degree).                    */
 /* core_out: the core estimates. Returns 0, or -1 on ENOMEM.                 */
 /* ------------------------------------------------------------------------ */
 static int32_t sampled_estimate(int64_t sel, int64_t sel0, int64_t d0, int32_t fallback)
@@ -585,12 +587,18 @@ int orc_peel_sampled(int32_t n, const int32_t *row_ptr, const int32_t *col, int3
             inB[v] = 0;
             core_out[v] = k;
             removed++;
+            int64_t blen = 0;
+            bfs_count(v, h, row_ptr, col, alive, dist, queue, ball, &blen);
             if (sampled_update(n, row_ptr, col, alive, in_s, h, v, sel, sel0, d0, est) < 0) {
                 free(d0); free(est); free(sel); free(sel0); free(alive); free(inB); free(dist); free(queue);
                 free(ball);
                 return -1;
             }
             alive[v] = 0;
+            /* members without a rate keep their exact h-degree */
+            for (int64_t i = 0; i < blen; i++)
+                if (sel0[ball[i]] == 0)
+                    est[ball[i]] = (int32_t)bfs_count(ball[i], h, row_ptr, col, alive, dist, queue, NULL, NULL);
             for (int32_t u = 0; u < n; u++)
                 if (alive[u] && !inB[u] && est[u] <= k) inB[u] = 1;
         }

@@ -463,3 +463,33 @@ def test_sampling_estimates_track_the_exact_cores():
         core, _ = oracle.peel_sampled(g, 2, (u < r).astype(np.uint8))
         err[r] = np.abs(core - exact).mean() / exact.mean()
     assert err[0.2] < 0.1 and err[0.95] < err[0.2] and err[1.0] == 0.0
+
+
+@pytest.mark.parametrize("h", [1, 2, 3])
+def test_sampling_vertices_without_a_sampled_neighbour_stay_exact(h):
+    """A component with no sampled vertex has no rate anywhere: its vertices
+    keep their exact h-degrees, so its estimated cores are Algorithm 1's; a
+    fully sampled component beside it is exact too (rate 1)."""
+    a, b = gg.chung_lu(150, 5.0, 2.3, 40.0, 61 + h), gg.erdos_renyi_gnm(120, 400, 62 + h)
+    g = gg.disjoint_union(a, b)
+    in_s = np.concatenate([np.zeros(a.n, np.uint8), np.ones(b.n, np.uint8)])
+    core, est = oracle.peel_sampled(g, h, in_s)
+    assert (core[: a.n] == oracle.peel(a, h)).all()
+    assert (core[a.n:] == oracle.peel(b, h)).all()
+    assert (est == oracle.hdegrees(g, h)).all()
+
+
+def test_sampled_cores_are_order_free():
+    """Each estimate is a monotone function of the surviving vertex set, so
+    the level-by-level peel gives the same estimated cores whatever the order
+    of deletions inside a level: relabelling the vertices (which changes the
+    order Algorithm 2 takes them in) permutes the result and nothing else."""
+    g = gg.chung_lu(400, 6.0, 2.4, 60.0, 63)
+    in_s = (gg.Stream(64, "sample").uniform(g.n) < 0.3).astype(np.uint8)
+    core, _ = oracle.peel_sampled(g, 2, in_s)
+    perm = np.argsort(gg.Stream(65, "perm").u64(g.n), kind="stable")
+    g2 = gg.relabel(g, perm)
+    s2 = np.zeros(g.n, np.uint8)
+    s2[perm] = in_s
+    core2, _ = oracle.peel_sampled(g2, 2, s2)
+    assert (core2[perm] == core).all()
