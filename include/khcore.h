@@ -225,6 +225,30 @@ khcore_status khcore_decompose_ex(khcore_ctx *ctx, int32_t h, int32_t *core_out,
                                   int32_t *round_out, khcore_stats *stats);
 
 /*
+ * khcore_decompose_sampled — the paper's sampling variant (Sec. IV-C,
+ * Algorithms 5 and 6): estimated core indices from a vertex sample S drawn by
+ * the caller (the paper draws r|V| vertices uniformly; the draw is an input
+ * here so that runs are reproducible).
+ *   in_s      uint8[n] (host or device): 1 = the vertex is in S
+ *   core_out  int32[n] (host or device): the estimated core indices
+ *   round_out, stats as for khcore_decompose_ex
+ * Every vertex v gets select0(v) = |N_v^h(G) cap S| and d0(v) = d_v^h(G);
+ * while peeling, select(v) = |N_v^h(G[alive]) cap S| and the estimated
+ * h-degree is floor(select * d0 / select0) (the paper's select / rate with
+ * rate = select0 / d0, in exact integers, rounded down as its example 8 /
+ * 0.45 -> 17 shows). A vertex with select0 = 0 has no rate and keeps its
+ * exact h-degree. The peel is Algorithm 2's on these estimates, level by
+ * level: each estimate only falls as vertices go, so the estimated cores do
+ * not depend on the order of deletions inside a level. S = V gives the exact
+ * core indices. Rounds are host-driven; the affected vertices of every round
+ * are recounted by the multi-source BFS, counting only sampled vertices (all
+ * vertices for the sources without a rate). One-graph contexts only (EINVAL
+ * otherwise).
+ */
+khcore_status khcore_decompose_sampled(khcore_ctx *ctx, int32_t h, const uint8_t *in_s, int32_t *core_out,
+                                      int32_t *round_out, khcore_stats *stats);
+
+/*
  * khcore_batch_create — one context holding G independent graphs (batching
  * many graphs of uneven size into the same kernel launches). The graphs are
  * packed: graph g has n_g = v_off[g+1] - v_off[g] vertices and

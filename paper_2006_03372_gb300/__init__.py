@@ -32,7 +32,7 @@ __all__ = [
     "khcore_status_string", "Stats",
     "KHCore", "library_path", "load_library", "khcore_batch_create", "khcore_batch_decompose", "pack_graphs",
     "khcore_hdegrees_of", "khcore_hdegrees_ex", "khcore_hdegrees_static", "Server", "request_bytes",
-    "khcore_set_update", "khcore_bitmap_update",
+    "khcore_set_update", "khcore_bitmap_update", "khcore_decompose_sampled",
 ]
 
 STATUS = {0: "KHCORE_OK", 1: "KHCORE_EINVAL", 2: "KHCORE_ENOMEM", 3: "KHCORE_ECUDA",
@@ -109,6 +109,8 @@ def load_library(build_if_missing: bool = False):
         lib.khcore_set_lazy.restype = ctypes.c_int
         lib.khcore_set_graph_blocks.argtypes = [P, i32]
         lib.khcore_set_graph_blocks.restype = ctypes.c_int
+        lib.khcore_decompose_sampled.argtypes = [P, i32, P, P, P, ctypes.POINTER(Stats)]
+        lib.khcore_decompose_sampled.restype = ctypes.c_int
         lib.khcore_set_update.argtypes = [P, i32]
         lib.khcore_set_update.restype = ctypes.c_int
         lib.khcore_bitmap_update.argtypes = [P, i32, P, i32, P, ctypes.POINTER(i64)]
@@ -245,6 +247,21 @@ def khcore_set_graph_blocks(ctx, mode: int) -> None:
     """0: automatic; 1: one thread block per whole graph; -1: grid-wide rounds only."""
     lib = load_library()
     _check(lib, ctx, lib.khcore_set_graph_blocks(ctx, int(mode)))
+
+
+def khcore_decompose_sampled(ctx, h: int, in_s, core_out=None, round_out=None, want_rounds: bool = True):
+    """(estimated core, round, stats) of the sampling variant (Algorithms 5
+    and 6) on the caller's sample in_s (uint8[n], 1 = sampled)."""
+    lib = load_library()
+    core = _out(ctx, core_out)
+    rnd = _out(ctx, round_out) if (want_rounds or round_out is not None) else None
+    a = np.ascontiguousarray(in_s, dtype=np.uint8) if not _is_torch(in_s) else in_s
+    pa, _ = _ptr(a, np.uint8)
+    pc, _ = _ptr(core)
+    pr, _ = _ptr(rnd)
+    stats = Stats()
+    _check(lib, ctx, lib.khcore_decompose_sampled(ctx, int(h), pa, pc, pr, ctypes.byref(stats)))
+    return core, rnd, stats.as_dict()
 
 
 def khcore_set_update(ctx, mode: int) -> None:

@@ -85,6 +85,14 @@ struct khcore_ctx {
     GridSync *gs = nullptr;
     PersistStats *pstats = nullptr;
     int32_t update_mode = 0;              // 0: BFS recompute; 1: the paper's per-deletion update (Algorithms 3/4)
+    // the sampling variant (Algorithms 5 and 6): sample bytes, select at the
+    // start and now, exact h-degrees at the start, the per-batch mask of the
+    // sources that count every vertex; sampling = 0 off, 1 select pass, 2 rounds
+    uint8_t *s_in = nullptr;
+    int32_t *s_sel0 = nullptr, *s_sel = nullptr, *s_d0 = nullptr;
+    uint64_t *s_full = nullptr;
+    int sampling = 0;
+    bool sampling_req = false;
     UpdBufs upd{};                        // its slots, allocated on first use
     bool upd_ready = false;
 
@@ -366,6 +374,13 @@ khcore_status hdeg_sources(khcore_ctx *c, int W, int32_t h, const int32_t *src, 
     b.boff = 0;
     b.wsum = wsum;
     b.wdeg = c->deg;
+    // sampling variant: 1 = the pass that counts the sampled vertices of every
+    // ball (select at the start), 2 = the rounds (estimates)
+    b.in_s = c->sampling ? c->s_in : nullptr;
+    b.fullmask = c->sampling ? c->s_full : nullptr;
+    b.sel0 = c->sampling == 2 ? c->s_sel0 : nullptr;
+    b.sel = c->sampling == 1 ? c->s_sel0 : (c->sampling == 2 ? c->s_sel : nullptr);
+    b.d0 = c->sampling == 2 ? c->s_d0 : nullptr;
     BfsTuning tune;
     tune.alpha = c->push_alpha;
     tune.n_alive = (int32_t)n_b;
@@ -762,8 +777,9 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
     pv.nDc = c->nDc;
     // the paper's per-deletion update (one graph): exact h-degrees after every
     // round (no bounds), host-driven rounds
-    const bool paper_update = c->update_mode == 1 && G == 1 && !(c->graph_blocks > 0);
-    const bool lazy = c->lazy && !paper_update;
+    const bool sampled = c->sampling_req && G == 1;
+    const bool paper_update = c->update_mode == 1 && G == 1 && !(c->graph_blocks > 0) && !sampled;
+    const bool lazy = c->lazy && !paper_update && !sampled;
     pv.slack = lazy ? c->slack : nullptr;
     pv.mind = lazy ? c->mind : nullptr;
     pv.minub = lazy ? c->minub : nullptr;
@@ -900,7 +916,26 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
     CU(cudaMemcpyAsync(&init_alg, c->alg, sizeof init_alg, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     stt.level_bytes = (double)init_alg;  // the initial pass
-    const int pgrid = (c->round_loop == 0 && !paper_update) ? c->sm_count * max_blocks_per_sm_persist(Wr) : 0;
+    if (sampled) {
+        // Algorithm 5: select = |N_v^h cap S| of every vertex (d0 = the exact
+        // h-degrees just computed), then the estimates start at d0
+        CU(cudaMemcpyAsync(c->s_d0, c->deg, sizeof(int32_t) * (size_t)c->n, cudaMemcpyDeviceToDevice, c->stream));
+        c->sampling = 1;
+        s = hdeg_sources(c, W, cls_h[0], c->cls_src, c->n, c->n, c->m, &stt);
+        c->sampling = 2;
+        if (s != KHCORE_OK) {
+            c->sampling = 0;
+            return s;
+        }
+        CU(launch_sample_init(c->s_sel0, c->s_d0, c->s_sel, c->n, c->stream));
+        stt.kernel_launches++;
+    }
+    struct SamplingOff {  // the context leaves sampling mode on every return
+        khcore_ctx *c;
+        ~SamplingOff() { c->sampling = 0; }
+    } sampling_off{c};
+    const int pgrid = (c->round_loop == 0 && !paper_update && !sampled) ? c->sm_count * max_blocks_per_sm_persist(Wr)
+                                                                          : 0;
     if (pgrid > 0) {
         // the whole decomposition in one cooperative launch
         PersistLaunch L;
@@ -939,6 +974,11 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         L.b.boff = 0;
         L.b.wsum = nullptr;
         L.b.wdeg = c->deg;
+        L.b.in_s = nullptr;
+        L.b.fullmask = nullptr;
+        L.b.sel0 = nullptr;
+        L.b.sel = nullptr;
+        L.b.d0 = nullptr;
         L.wsum = lazy ? c->wsum : nullptr;
         L.vis = c->vis;
         L.A = c->src;
@@ -1082,7 +1122,9 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         // or 1 when a single vertex went.
         for (int32_t k = 0; k < ncls; k++) {
             const int32_t na = c->nAc_host[k];
-            const int32_t ni = std::min(c->nAc_host[G + k], na);
+            // sampling: every affected vertex is recounted (its estimate
+            // depends on which sampled vertices it still reaches)
+            const int32_t ni = sampled ? na : std::min(c->nAc_host[G + k], na);
             const int32_t nd = c->nAc_host[2 * G + k];
             if (na == 0) continue;
             const bool single = (ps.nD == 1);  // every affected vertex loses exactly that one
@@ -1192,6 +1234,8 @@ void khcore_destroy(khcore_ctx *c)
                     c->Fx, c->flagx, c->tflag, c->flag[0], c->flag[1], c->Q[0], c->Q[1], c->Q[2], c->I[0], c->I[1], c->I[2], c->T, c->ctl,
                     c->cnt, c->edges, c->alg};
     for (void *p : bufs) cudaFree(p);
+    void *sbufs[] = {c->s_in, c->s_sel0, c->s_sel, c->s_d0, c->s_full};
+    for (void *p : sbufs) cudaFree(p);
     void *ubufs[] = {c->upd.vis, c->upd.list, c->upd.dist, c->upd.reach, c->upd.meta, c->upd.owner, c->upd.lab,
                      c->upd.done, c->upd.flag, c->upd.cand[0], c->upd.cand[1]};
     for (void *p : ubufs) cudaFree(p);
@@ -1513,6 +1557,32 @@ khcore_status khcore_decompose_ex(khcore_ctx *c, int32_t h, int32_t *core_out, i
 khcore_status khcore_decompose(khcore_ctx *c, int32_t h, int32_t *core_out)
 {
     return khcore_decompose_ex(c, h, core_out, nullptr, nullptr);
+}
+
+khcore_status khcore_decompose_sampled(khcore_ctx *c, int32_t h, const uint8_t *in_s, int32_t *core_out,
+                                      int32_t *round_out, khcore_stats *stats)
+{
+    khcore_status s;
+    if ((s = check_ctx(c)) != KHCORE_OK) return s;
+    if (h < 1) return fail(c, KHCORE_EINVAL, "h must be >= 1 (got %d)", h);
+    if (c->G != 1) return fail(c, KHCORE_EINVAL, "khcore_decompose_sampled takes a one-graph context");
+    if (!in_s && c->n > 0) return fail(c, KHCORE_EINVAL, "in_s must not be NULL");
+    const size_t n = (size_t)std::max(c->n, 1);
+    if (!c->s_in) {
+        CU(dev_alloc(&c->s_in, n));
+        CU(dev_alloc(&c->s_sel0, n));
+        CU(dev_alloc(&c->s_sel, n));
+        CU(dev_alloc(&c->s_d0, n));
+        CU(dev_alloc(&c->s_full, 16));
+        CU(cudaMemsetAsync(c->s_full, 0, 16 * sizeof(uint64_t), c->stream));
+    }
+    if (c->n > 0)
+        CU(cudaMemcpyAsync(c->s_in, in_s, (size_t)c->n,
+                           is_device_ptr(in_s) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    c->sampling_req = true;
+    s = decompose(c, std::vector<int32_t>{h}, core_out, round_out, stats);
+    c->sampling_req = false;
+    return s;
 }
 
 khcore_status khcore_batch_decompose(khcore_ctx *c, const int32_t *h, int32_t *core_out, int32_t *round_out,

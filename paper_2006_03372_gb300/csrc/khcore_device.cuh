@@ -150,13 +150,18 @@ __device__ __forceinline__ uint64_t row_mask(int j, int32_t row_first)
 
 // Bits of word j that a vertex y may count for (see BfsBufs::slev): source
 // positions below cum[hcnt - slev[y]]; every bit when no eligibility is set.
+// With sampling (b.in_s), an unsampled vertex counts only for the sources
+// of b.fullmask.
 __device__ __forceinline__ uint64_t elig_mask(const BfsBufs &b, int j, int32_t y)
 {
-    if (!b.slev || y < 0) return ~0ull;
-    const int32_t lim = b.cum[b.hcnt - b.slev[y]] - b.boff - 64 * j;
-    if (lim <= 0) return 0ull;
-    if (lim >= 64) return ~0ull;
-    return (1ull << lim) - 1ull;
+    if (y < 0) return ~0ull;
+    uint64_t m = ~0ull;
+    if (b.slev) {
+        const int32_t lim = b.cum[b.hcnt - b.slev[y]] - b.boff - 64 * j;
+        m = lim <= 0 ? 0ull : (lim >= 64 ? ~0ull : (1ull << lim) - 1ull);
+    }
+    if (b.in_s && !b.in_s[y]) m &= b.fullmask[j];
+    return m;
 }
 
 // Per-thread accumulators flushed once at the end of a level kernel.
@@ -302,6 +307,9 @@ __device__ __forceinline__ void dev_seed(const int32_t *src, int32_t ns, BfsBufs
         b.F[0][(size_t)s * W + word] = bit;  // F rows are zero between batches
         b.flag[0][s] = 1;
         b.T[i] = s;
+        // sampling: sources without a rate count every vertex they reach
+        if (b.in_s && b.sel0 && b.sel0[s] == 0)
+            atomicOr(reinterpret_cast<unsigned long long *>(&b.fullmask[word]), (unsigned long long)bit);
     }
     Acc dummy{0, 0, 0};
     append_frontier<W>(i < ns, s, (int32_t)d, b, 0, dummy, rp);  // Q[0] and the level-0 push items
@@ -749,9 +757,19 @@ __device__ __forceinline__ void dev_end(BfsBufs b, const int32_t *src, int32_t n
         if (idx < nt) b.V[(size_t)b.T[idx] * W + j] = 0;
     }
     if (tid < ns) {
-        deg[src[tid]] = b.cnt[tid];
+        const int32_t s = src[tid], c = b.cnt[tid];
+        if (b.sel) {
+            b.sel[s] = c;
+            if (b.sel0) {
+                const int32_t s0 = b.sel0[s];
+                deg[s] = s0 > 0 ? (c > 0 ? (int32_t)((long long)c * b.d0[s] / s0) : 0) : c;
+            }
+        } else {
+            deg[s] = c;
+        }
         b.cnt[tid] = 0;
     }
+    if (b.fullmask && tid < W) b.fullmask[tid] = 0;
 }
 
 

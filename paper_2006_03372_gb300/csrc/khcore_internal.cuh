@@ -110,6 +110,19 @@ struct BfsBufs {
     // dev_weight_pass); wdeg holds the sources' h-degree bounds.
     int32_t *wsum;
     const int32_t *wdeg;
+    // Optional sampling (the paper's sampling variant, Algorithms 5 and 6;
+    // per-phase kernels only): when in_s is set, a source counts only the
+    // sampled vertices it reaches (in_s[y] != 0), except the sources whose
+    // bit is set in fullmask (W words, filled by the seed from sel0: those
+    // with sel0 == 0 count every vertex). At the end of the batch the count
+    // of source s goes to sel[s]; when sel0 is set too, deg[s] receives the
+    // estimate floor(count * d0[s] / sel0[s]) (the count itself when
+    // sel0[s] == 0), otherwise deg is left alone.
+    const uint8_t *in_s;
+    uint64_t *fullmask;
+    const int32_t *sel0;
+    int32_t *sel;
+    const int32_t *d0;
 };
 
 // Direction choice of one level: push when (sum of frontier degrees) * alpha
@@ -208,6 +221,8 @@ cudaError_t launch_min_over_list(const int32_t *list, int32_t count, const int32
 cudaError_t launch_apply_lazy(const int32_t *list, int32_t inner, int32_t total, int32_t *dcount, int32_t *deg,
                               int32_t *slack, int32_t extra, int32_t *wsum, const int32_t *d1, const int32_t *rp,
                               int32_t h, cudaStream_t s);
+// Sampling variant: sel[i] = sel0[i] > 0 ? sel0[i] : d0[i].
+cudaError_t launch_sample_init(const int32_t *sel0, const int32_t *d0, int32_t *sel, int32_t n, cudaStream_t s);
 // dst = a[0..na) followed by b[0..nb).
 cudaError_t launch_concat(int32_t *dst, const int32_t *a, int32_t na, const int32_t *b, int32_t nb, cudaStream_t s);
 // st->nA = sum of p.nAc.

@@ -56,6 +56,13 @@ __global__ void k_concat(int32_t *dst, const int32_t *a, int32_t na, const int32
 {
     dev_concat(dst, a, na, b, nb);
 }
+// Sampling variant: the running select count starts at select0, or at the
+// exact h-degree for a vertex without a rate (select0 = 0).
+__global__ void k_sample_init(const int32_t *sel0, const int32_t *d0, int32_t *sel, int32_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        sel[i] = sel0[i] > 0 ? sel0[i] : d0[i];
+}
 
 }  // namespace
 
@@ -159,6 +166,13 @@ cudaError_t launch_apply_lazy(const int32_t *list, int32_t inner, int32_t total,
 cudaError_t launch_sum_classes(const PeelView &p, PeelState *st, cudaStream_t s)
 {
     k_sum_classes<<<1, 1, 0, s>>>(p, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_init(const int32_t *sel0, const int32_t *d0, int32_t *sel, int32_t n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_sample_init<<<(n + 255) / 256 < 2048 ? (n + 255) / 256 : 2048, 256, 0, s>>>(sel0, d0, sel, n);
     return cudaGetLastError();
 }
 

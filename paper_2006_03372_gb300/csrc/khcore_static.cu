@@ -259,6 +259,11 @@ extern "C" khcore_status khcore_hdegrees_static(int32_t n, int64_t m, const int3
     b.boff = 0;
     b.wsum = nullptr;
     b.wdeg = nullptr;
+    b.in_s = nullptr;
+    b.fullmask = nullptr;
+    b.sel0 = nullptr;
+    b.sel = nullptr;
+    b.d0 = nullptr;
     BfsTuning tune;
     tune.alpha = 16;
     tune.n_alive = n;
