@@ -180,7 +180,7 @@ khcore_status khcore_hdegrees_of(khcore_ctx *ctx, int32_t h, int32_t count, cons
  *   deg_out  int32[count], device: deg_out[i] = d^h of verts[i] in G
  *   stream   cudaStream_t the work is ordered on (NULL: the legacy default
  *            stream)
- * Limit: the scratch needs about 74 n + 0.2 m bytes (exactly: 256-byte
+ * Limit: the scratch needs about 73 n + 0.75 m bytes (exactly: 256-byte
  * aligned regions of the multi-source BFS at 64 sources per batch); larger
  * graphs are rejected with KHCORE_EINVAL and a message naming the bytes
  * needed, before any device work. Offsets that are not a CSR, ids out of

@@ -62,9 +62,9 @@ struct khcore_ctx {
     int Wr_req = 0;  // W of the peel rounds, 0 = automatic
     int W_alloc = 0;
     uint64_t *V = nullptr, *F[2] = {nullptr, nullptr};
-    uint8_t *flag[2] = {nullptr, nullptr};
+    uint32_t *flag[2] = {nullptr, nullptr};  // frontier bitmaps
     uint64_t *Fx = nullptr;                    // third frontier array of the persistent kernel's ring
-    uint8_t *flagx = nullptr, *tflag = nullptr;  // its flags; vertices already in the touched list
+    uint32_t *flagx = nullptr, *tflag = nullptr;  // its flag bitmap; vertices already in the touched list
     int32_t *Q[3] = {nullptr, nullptr, nullptr};
     int2 *I[3] = {nullptr, nullptr, nullptr};
     int32_t *T = nullptr;
@@ -304,7 +304,7 @@ khcore_status clear_if_dirty(khcore_ctx *c)
 {
     if (!c->dirty || c->W_alloc == 0) return KHCORE_OK;
     const size_t words = (size_t)std::max(c->n, 1) * c->W_alloc;
-    const size_t nflag = (((size_t)c->n + 3) / 4) * 4;
+    const size_t nflag = (((size_t)c->n + 31) / 32) * 4;  // bytes of one flag bitmap
     CU(cudaMemsetAsync(c->V, 0, words * sizeof(uint64_t), c->stream));
     CU(cudaMemsetAsync(c->F[0], 0, words * sizeof(uint64_t), c->stream));
     CU(cudaMemsetAsync(c->F[1], 0, words * sizeof(uint64_t), c->stream));
@@ -460,7 +460,7 @@ khcore_status setup_ctx(khcore_ctx *c, const std::vector<int32_t> &rp, const std
         else c->n_heavy++;
     }
     const size_t nw = ((size_t)n + 31) / 32;
-    const size_t nflag = (((size_t)n + 3) / 4) * 4;  // whole 32-bit words (flag claims)
+    const size_t nflag = (((size_t)n + 31) / 32) * 4;  // bytes of one frontier flag bitmap
     khcore_status st = KHCORE_OK;
     auto A = [&](cudaError_t e2) {
         if (e2 != cudaSuccess && st == KHCORE_OK) {
@@ -482,10 +482,10 @@ khcore_status setup_ctx(khcore_ctx *c, const std::vector<int32_t> &rp, const std
     A(dev_alloc(&c->st, 1));
     A(dev_alloc(&c->edges, 1));
     A(dev_alloc(&c->alg, 1));
-    A(dev_alloc(&c->flag[0], nflag));
-    A(dev_alloc(&c->flag[1], nflag));
-    A(dev_alloc(&c->flagx, nflag));
-    A(dev_alloc(&c->tflag, nflag));
+    A(dev_alloc(&c->flag[0], nflag / 4));
+    A(dev_alloc(&c->flag[1], nflag / 4));
+    A(dev_alloc(&c->flagx, nflag / 4));
+    A(dev_alloc(&c->tflag, nflag / 4));
     for (int k = 0; k < 3; k++) {
         A(dev_alloc(&c->Q[k], (size_t)n));
         // push items: every frontier row in chunks of at least 8 entries

@@ -74,12 +74,16 @@ __device__ __forceinline__ void warp_append(bool pred, int32_t val, int32_t *lis
     if (pred) list[base + __popc(m & lanemask_lt())] = val;
 }
 
-// Byte test-and-set on a uint8 flag array through its 32-bit word.
-__device__ __forceinline__ bool flag_claim(uint8_t *flags, int32_t y)
+// Frontier flags, one bit per vertex (n/8 bytes: the pull direction tests a
+// flag for every CSR entry it scans, and a bitmap keeps those tests in L1).
+__device__ __forceinline__ bool flag_test(const uint32_t *f, int32_t y) { return (f[y >> 5] >> (y & 31)) & 1u; }
+__device__ __forceinline__ void flag_set(uint32_t *f, int32_t y) { atomicOr(&f[y >> 5], 1u << (y & 31)); }
+__device__ __forceinline__ void flag_clear(uint32_t *f, int32_t y) { atomicAnd(&f[y >> 5], ~(1u << (y & 31))); }
+// Test-and-set: true for the one caller that set the bit.
+__device__ __forceinline__ bool flag_claim(uint32_t *f, int32_t y)
 {
-    unsigned *word = reinterpret_cast<unsigned *>(flags + (y & ~3));
-    const unsigned bit = 1u << (8 * (y & 3));
-    return (atomicOr(word, bit) & bit) == 0;
+    const uint32_t bit = 1u << (y & 31);
+    return (atomicOr(&f[y >> 5], bit) & bit) == 0;
 }
 
 // Byte-sliced column counters: byte k of a[t] counts bit 8k+t of the words
@@ -238,21 +242,21 @@ __device__ __forceinline__ void or_row(uint64_t (&a)[W], const uint64_t *F, int3
 // col -> flag -> row chains in flight.
 template <int W>
 __device__ __forceinline__ void gather_edges(uint64_t (&a)[W], const int32_t *col,
-                                             const uint8_t *flc, const uint64_t *Fc,
+                                             const uint32_t *flc, const uint64_t *Fc,
                                              int32_t first, int32_t e1, int32_t stride)
 {
     int32_t e = first;
     for (; e + stride < e1; e += 2 * stride) {
         const int32_t x0 = __ldg(&col[e]);
         const int32_t x1 = __ldg(&col[e + stride]);
-        const uint8_t f0 = flc[x0];
-        const uint8_t f1 = flc[x1];
+        const bool f0 = flag_test(flc, x0);
+        const bool f1 = flag_test(flc, x1);
         if (f0) or_row<W>(a, Fc, x0);
         if (f1) or_row<W>(a, Fc, x1);
     }
     if (e < e1) {
         const int32_t x0 = __ldg(&col[e]);
-        if (flc[x0]) or_row<W>(a, Fc, x0);
+        if (flag_test(flc, x0)) or_row<W>(a, Fc, x0);
     }
 }
 
@@ -305,7 +309,7 @@ __device__ __forceinline__ void dev_seed(const int32_t *src, int32_t ns, BfsBufs
         const uint64_t bit = 1ull << (i & 63);
         b.V[(size_t)s * W + word] = bit;  // V(s) is zero between batches
         b.F[0][(size_t)s * W + word] = bit;  // F rows are zero between batches
-        b.flag[0][s] = 1;
+        flag_set(b.flag[0], s);
         b.T[i] = s;
         // sampling: sources without a rate count every vertex they reach
         if (b.in_s && b.sel0 && b.sel0[s] == 0)
@@ -330,7 +334,7 @@ __device__ __forceinline__ void dev_seed(const int32_t *src, int32_t ns, BfsBufs
 template <int W, int G>
 __device__ __forceinline__ void finish_vertex(bool act, int32_t y, int32_t dy, uint64_t nw, uint64_t v, int gi,
                                               int grp, uint64_t *V, uint64_t *Fn,
-                                              uint8_t *fln, const BfsBufs &b, int nslot, Acc &acc,
+                                              uint32_t *fln, const BfsBufs &b, int nslot, Acc &acc,
                                               const int32_t *rp)
 {
     const unsigned gmask = (G == 32) ? kFull : ((1u << G) - 1u);
@@ -344,9 +348,9 @@ __device__ __forceinline__ void finish_vertex(bool act, int32_t y, int32_t dy, u
         acc.scanned += (unsigned long long)__popcll(nw) * (unsigned long long)dy;
     }
     const bool lead = act && gany && gi == 0;
-    if (lead) fln[y] = 1;
+    if (lead) flag_set(fln, y);
     append_frontier<W>(lead, y, dy, b, nslot, acc, rp);
-    if (b.tflag && lead && !gv) b.tflag[y] = 1;  // first visit (fused levels keep T by tflag)
+    if (b.tflag && lead && !gv) flag_set(b.tflag, y);  // first visit (fused levels keep T by tflag)
     warp_append(lead && !gv, y, b.T, &b.ctl->t);
 }
 
@@ -355,8 +359,8 @@ template <int W, int G, bool LAST>
 __device__ __forceinline__ void pull_groups(const int32_t *list, int32_t count, int64_t warp,
                                             int64_t nwarps, const GraphView &g, const uint32_t *alive,
                                             uint64_t *V, const uint64_t *Fc,
-                                            const uint8_t *flc, uint64_t *Fn,
-                                            uint8_t *fln, const BfsBufs &b, int nslot, Swar &sw,
+                                            const uint32_t *flc, uint64_t *Fn,
+                                            uint32_t *fln, const BfsBufs &b, int nslot, Swar &sw,
                                             int32_t *cnt_s, Acc &acc)
 {
     static_assert(G >= W && 32 % G == 0, "group");
@@ -436,13 +440,13 @@ __device__ __forceinline__ void clear_slot(const BfsBufs &b, int slot)
     const int32_t nq = b.ctl->q[slot];
     const int32_t *Qs = pick3(b.Q, slot);
     uint64_t *Fs = ring3(b.F[0], b.F[1], b.Fx, slot);
-    uint8_t *fls = ring3(b.flag[0], b.flag[1], b.flagx, slot);
+    uint32_t *fls = ring3(b.flag[0], b.flag[1], b.flagx, slot);
     for (int64_t base = warp * VPW; base < nq; base += nwarps * VPW) {
         const int64_t idx = base + grp;
         if (idx < nq) {
             const int32_t x = Qs[idx];
             Fs[(size_t)x * W + j] = 0;
-            if (j == 0) fls[x] = 0;
+            if (j == 0) flag_clear(fls, x);
         }
     }
 }
@@ -458,9 +462,9 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
     const int cslot = lvl % 3, nslot = (lvl + 1) % 3;
     const int cb = lvl & 1, nb_ = cb ^ 1;
     const uint64_t *Fc = FUSED ? ring3(b.F[0], b.F[1], b.Fx, cslot) : pick2(b.F, cb);
-    const uint8_t *flc = FUSED ? ring3(b.flag[0], b.flag[1], b.flagx, cslot) : pick2(b.flag, cb);
+    const uint32_t *flc = FUSED ? ring3(b.flag[0], b.flag[1], b.flagx, cslot) : pick2(b.flag, cb);
     uint64_t *Fn = FUSED ? ring3(b.F[0], b.F[1], b.Fx, nslot) : pick2(b.F, nb_);
-    uint8_t *fln = FUSED ? ring3(b.flag[0], b.flag[1], b.flagx, nslot) : pick2(b.flag, nb_);
+    uint32_t *fln = FUSED ? ring3(b.flag[0], b.flag[1], b.flagx, nslot) : pick2(b.flag, nb_);
     uint64_t *V = b.V;
     const bool push = use_push(b.ctl, cslot, tune);
 
@@ -663,8 +667,8 @@ __device__ __forceinline__ void dev_post(GraphView g, BfsBufs b, int lvl, BfsTun
     const int32_t *Qn = pick3(b.Q, nslot);
     uint64_t *Fc = pick2(b.F, cb);
     uint64_t *Fn = pick2(b.F, nb_);
-    uint8_t *flc = pick2(b.flag, cb);
-    uint8_t *fln = pick2(b.flag, nb_);
+    uint32_t *flc = pick2(b.flag, cb);
+    uint32_t *fln = pick2(b.flag, nb_);
 
     // clear the expanded frontier's rows
     for (int64_t base = warp * VPW; base < nq; base += nwarps * VPW) {
@@ -672,7 +676,7 @@ __device__ __forceinline__ void dev_post(GraphView g, BfsBufs b, int lvl, BfsTun
         if (idx < nq) {
             const int32_t x = Qc[idx];
             Fc[(size_t)x * W + j] = 0;
-            if (j == 0) flc[x] = 0;
+            if (j == 0) flag_clear(flc, x);
         }
     }
     if (push) {
@@ -685,7 +689,7 @@ __device__ __forceinline__ void dev_post(GraphView g, BfsBufs b, int lvl, BfsTun
                 f = Fn[(size_t)y * W + j];
                 if (LAST) {
                     Fn[(size_t)y * W + j] = 0;
-                    if (j == 0) fln[y] = 0;
+                    if (j == 0) flag_clear(fln, y);
                 } else {
                     v = b.V[(size_t)y * W + j];
                     if (f) b.V[(size_t)y * W + j] = v | f;
@@ -803,7 +807,7 @@ __device__ __forceinline__ void dev_end_fused(const BfsBufs &b, const int32_t *s
             const int32_t u = b.T[idx];
             b.V[(size_t)u * W + j] = 0;
             if (j == 0) {
-                b.tflag[u] = 0;
+                flag_clear(b.tflag, u);
                 if (slack && is_alive(alive, u)) {
                     const int32_t d = deg[u];
                     const int32_t ex = min(nt, b.wsum ? b.wsum[u] : nt);

@@ -64,7 +64,7 @@ __host__ __device__ constexpr int push_chunk(int W) { return (32 / W) > 8 ? 32 /
 //            except those listed in T
 //   F[2]     frontier words of the current / next level; a row is nonzero
 //            only while its vertex is in that level's list Q
-//   flag[2]  one byte per vertex: 1 iff the vertex is in that frontier
+//   flag[2]  one bit per vertex: set iff the vertex is in that frontier
 //   Q[3], I[3], T   frontier lists and their push work items (ring of three),
 //                   touched-row list
 //   ctl      list lengths and frontier degree sums
@@ -78,13 +78,13 @@ __host__ __device__ constexpr int push_chunk(int W) { return (32 / W) > 8 ? 32 /
 struct BfsBufs {
     uint64_t *V;
     uint64_t *F[2];
-    uint8_t *flag[2];
+    uint32_t *flag[2];
     // Fused levels (persistent kernel) only: the third frontier array and
-    // flag array of the three-slot ring, and one byte per vertex marking the
+    // flag bitmap of the three-slot ring, and one bit per vertex marking the
     // vertices already in T (all zero between batches).
     uint64_t *Fx;
-    uint8_t *flagx;
-    uint8_t *tflag;
+    uint32_t *flagx;
+    uint32_t *tflag;
     int32_t *Q[3];
     int2 *I[3];
     int32_t *T;

@@ -167,8 +167,8 @@ __device__ bool bfs_batch(const PersistArgs &a, const int32_t *src, int32_t ns, 
                 const uint64_t bit = 1ull << (i & 63);
                 b.V[(size_t)s * W + word] = bit;     // V rows are zero between batches
                 b.F[0][(size_t)s * W + word] = bit;  // so are F rows
-                b.flag[0][s] = 1;
-                b.tflag[s] = 1;
+                flag_set(b.flag[0], s);
+                flag_set(b.tflag, s);
                 b.T[i] = s;
             }
             Acc acc0{0, 0, 0};

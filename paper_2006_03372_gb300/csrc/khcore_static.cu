@@ -52,7 +52,7 @@ struct StaticLayout {
     {
         const size_t nn = (size_t)(n > 0 ? n : 1);
         const size_t nw = (nn + 31) / 32;
-        const size_t nflag = ((nn + 3) / 4) * 4;
+        const size_t nflag = nw * sizeof(uint32_t);  // one frontier flag bitmap
         const size_t items = nn + (size_t)m / push_chunk(kStaticW) + 1;
         size_t o = 0;
         auto take = [&](size_t bytes) {
@@ -235,8 +235,8 @@ extern "C" khcore_status khcore_hdegrees_static(int32_t n, int64_t m, const int3
     b.V = (uint64_t *)(base + L.V);
     b.F[0] = (uint64_t *)(base + L.F0);
     b.F[1] = (uint64_t *)(base + L.F1);
-    b.flag[0] = base + L.flag0;
-    b.flag[1] = base + L.flag1;
+    b.flag[0] = (uint32_t *)(base + L.flag0);
+    b.flag[1] = (uint32_t *)(base + L.flag1);
     for (int k = 0; k < 3; k++) {
         b.Q[k] = (int32_t *)(base + L.Q[k]);
         b.I[k] = (int2 *)(base + L.I[k]);
