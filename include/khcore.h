@@ -83,10 +83,13 @@ typedef struct {
     int64_t level_launches;    /* level kernel launches timed */
     double level_ms;           /* their summed device time (CUDA events) */
     double level_bytes;        /* algorithmic bytes of the initial pass's levels.
-                                  Per level, pull: 4*n_b + 4*m_b + 16*W*n_b for
-                                  the n_b alive rows and their m_b CSR entries;
-                                  push: (4 + 16*W) per frontier CSR entry plus
-                                  8*W per frontier vertex */
+                                  Per level, pull: 4*n_b + 4*m_b for the n_b
+                                  alive rows and their m_b CSR entries, 8*W per
+                                  frontier entry gathered and 16*W per vertex
+                                  with a frontier neighbour (own visited row
+                                  read, next-frontier row written); push:
+                                  (4 + 16*W) per frontier CSR entry plus 8*W per
+                                  frontier vertex */
     int64_t recomputed_total;  /* affected vertices whose h-degree was recomputed
                                   by BFS (those closer than h to the deleted set);
                                   the others were updated by counting */
@@ -321,6 +324,65 @@ khcore_status khcore_set_push_alpha(khcore_ctx *ctx, int32_t alpha);
  * closer than h to the deleted set in every round).
  */
 khcore_status khcore_set_lazy(khcore_ctx *ctx, int32_t on);
+
+/*
+ * Tuning knobs. None of them changes a result; each changes only how the
+ * kernels cut up the work.
+ *
+ * khcore_set_degree_classes — degree classes of the pull direction of the
+ * multi-source BFS: a vertex with at most light_max CSR entries is gathered by
+ * a group of max(8, W) lanes, one with at most medium_max by a warp, a larger
+ * one by a whole thread block (defaults 32 and 1024). EINVAL unless
+ * 0 <= light_max <= medium_max.
+ */
+khcore_status khcore_set_degree_classes(khcore_ctx *ctx, int32_t light_max, int32_t medium_max);
+
+/* khcore_set_block_size — threads per block of the per-phase BFS kernels
+ * (the all-vertex pass and the host-driven rounds): 128, 256 or 512 (the
+ * default); EINVAL otherwise. The persistent round kernel keeps 512. */
+khcore_status khcore_set_block_size(khcore_ctx *ctx, int32_t threads);
+
+/* khcore_set_block_graph_max — batch contexts: graphs of at most nmax
+ * vertices are decomposed by one thread block each (default 4096; see
+ * khcore_set_graph_blocks). EINVAL for nmax < 0. */
+khcore_status khcore_set_block_graph_max(khcore_ctx *ctx, int32_t nmax);
+
+/* The knobs khcore_autotune chose. */
+typedef struct {
+    int32_t words;            /* W of the all-vertex pass (khcore_set_words) */
+    int32_t block;            /* khcore_set_block_size */
+    int32_t light_max;        /* khcore_set_degree_classes */
+    int32_t medium_max;
+    int32_t push_alpha;       /* khcore_set_push_alpha */
+    int32_t block_graph_max;  /* khcore_set_block_graph_max */
+    int32_t from_cache;       /* 1: read from the cache file, nothing measured */
+    int32_t trials;           /* settings timed */
+    double trial_ms;          /* device time of the timed trials */
+} khcore_tuning;
+
+/*
+ * khcore_autotune — pick the knobs above for this context's graph, GPU and h
+ * by measurement, and apply them.
+ *   One-graph contexts: the multi-source BFS is timed (CUDA events) on the
+ *   first min(n, 4096) vertices as sources, knob by knob (W in {4, 8, 16},
+ *   block size in {128, 256, 512}, light_max in {16, 32, 64}, medium_max in
+ *   {256, 1024, 4096}, push alpha in {4, 16, 64}), each set to its fastest
+ *   value before the next is tried; every trial's h-degrees must agree
+ *   (KHCORE_EINTERNAL otherwise).
+ *   Batch contexts: block_graph_max, from up to 8 graphs of 512 to 32,768
+ *   vertices each decomposed alone on one thread block and on the whole
+ *   grid: the largest size where one block was not slower.
+ *   cache_path  NULL, or a file of JSON lines keyed by the GPU name, the
+ *               number of graphs, log2 of n, m and the largest degree, and
+ *               the effective h. A matching line is applied without any
+ *               measurement (from_cache = 1); otherwise the choice is
+ *               appended to the file.
+ *   out         khcore_tuning* or NULL
+ * The round W (khcore_set_round_words) is left to its automatic choice: the
+ * rounds' BFS batches are small and latency-bound, and timing them needs
+ * whole decompositions.
+ */
+khcore_status khcore_autotune(khcore_ctx *ctx, int32_t h, const char *cache_path, khcore_tuning *out);
 
 /*
  * khcore_set_update — how the h-degrees are brought up to date after a

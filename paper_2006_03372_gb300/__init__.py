@@ -32,12 +32,23 @@ __all__ = [
     "khcore_status_string", "Stats",
     "KHCore", "library_path", "load_library", "khcore_batch_create", "khcore_batch_decompose", "pack_graphs",
     "khcore_hdegrees_of", "khcore_hdegrees_ex", "khcore_hdegrees_static", "Server", "request_bytes",
-    "khcore_set_update", "khcore_bitmap_update", "khcore_decompose_sampled",
+    "khcore_set_update", "khcore_bitmap_update", "khcore_decompose_sampled", "khcore_set_degree_classes",
+    "khcore_set_block_size", "khcore_set_block_graph_max", "khcore_autotune", "Tuning",
 ]
 
 STATUS = {0: "KHCORE_OK", 1: "KHCORE_EINVAL", 2: "KHCORE_ENOMEM", 3: "KHCORE_ECUDA",
           4: "KHCORE_ETIMEOUT", 5: "KHCORE_EBUSY", 6: "KHCORE_EINTERNAL"}
 FLAG_TRUST_INPUT = 0x1
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("words", ctypes.c_int32), ("block", ctypes.c_int32), ("light_max", ctypes.c_int32),
+                ("medium_max", ctypes.c_int32), ("push_alpha", ctypes.c_int32),
+                ("block_graph_max", ctypes.c_int32), ("from_cache", ctypes.c_int32), ("trials", ctypes.c_int32),
+                ("trial_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class KHCoreError(RuntimeError):
@@ -111,6 +122,14 @@ def load_library(build_if_missing: bool = False):
         lib.khcore_set_graph_blocks.restype = ctypes.c_int
         lib.khcore_decompose_sampled.argtypes = [P, i32, P, P, P, ctypes.POINTER(Stats)]
         lib.khcore_decompose_sampled.restype = ctypes.c_int
+        lib.khcore_set_degree_classes.argtypes = [P, i32, i32]
+        lib.khcore_set_degree_classes.restype = ctypes.c_int
+        lib.khcore_set_block_size.argtypes = [P, i32]
+        lib.khcore_set_block_size.restype = ctypes.c_int
+        lib.khcore_set_block_graph_max.argtypes = [P, i32]
+        lib.khcore_set_block_graph_max.restype = ctypes.c_int
+        lib.khcore_autotune.argtypes = [P, i32, ctypes.c_char_p, ctypes.POINTER(Tuning)]
+        lib.khcore_autotune.restype = ctypes.c_int
         lib.khcore_set_update.argtypes = [P, i32]
         lib.khcore_set_update.restype = ctypes.c_int
         lib.khcore_bitmap_update.argtypes = [P, i32, P, i32, P, ctypes.POINTER(i64)]
@@ -262,6 +281,31 @@ def khcore_decompose_sampled(ctx, h: int, in_s, core_out=None, round_out=None, w
     stats = Stats()
     _check(lib, ctx, lib.khcore_decompose_sampled(ctx, int(h), pa, pc, pr, ctypes.byref(stats)))
     return core, rnd, stats.as_dict()
+
+
+def khcore_set_degree_classes(ctx, light_max: int, medium_max: int) -> None:
+    lib = load_library()
+    _check(lib, ctx, lib.khcore_set_degree_classes(ctx, int(light_max), int(medium_max)))
+
+
+def khcore_set_block_size(ctx, threads: int) -> None:
+    lib = load_library()
+    _check(lib, ctx, lib.khcore_set_block_size(ctx, int(threads)))
+
+
+def khcore_set_block_graph_max(ctx, nmax: int) -> None:
+    lib = load_library()
+    _check(lib, ctx, lib.khcore_set_block_graph_max(ctx, int(nmax)))
+
+
+def khcore_autotune(ctx, h: int, cache_path=None) -> dict:
+    """Measure and apply the tuning knobs for this graph, GPU and h (see
+    include/khcore.h); returns the chosen values."""
+    lib = load_library()
+    t = Tuning()
+    p = None if cache_path is None else os.fsencode(cache_path)
+    _check(lib, ctx, lib.khcore_autotune(ctx, int(h), p, ctypes.byref(t)))
+    return t.as_dict()
 
 
 def khcore_set_update(ctx, mode: int) -> None:

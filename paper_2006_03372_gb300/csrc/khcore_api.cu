@@ -85,6 +85,12 @@ struct khcore_ctx {
     GridSync *gs = nullptr;
     PersistStats *pstats = nullptr;
     int32_t update_mode = 0;              // 0: BFS recompute; 1: the paper's per-deletion update (Algorithms 3/4)
+    // tuning knobs (khcore_autotune picks them)
+    int32_t light_max = kLightMax;        // pull degree classes
+    int32_t medium_max = kMediumMax;
+    int32_t block = kBlock;               // threads per block of the per-phase BFS kernels
+    int32_t block_graph_max = kBlockGraphsMaxN;  // batches: graphs decomposed by one thread block
+    int32_t *class_counts = nullptr;      // [6] scratch of the class builder
     // the sampling variant (Algorithms 5 and 6): sample bytes, select at the
     // start and now, exact h-degrees at the start, the per-batch mask of the
     // sources that count every vertex; sampling = 0 off, 1 select pass, 2 rounds
@@ -296,7 +302,7 @@ khcore_status ensure_bfs(khcore_ctx *c, int W)
     return KHCORE_OK;
 }
 
-int bfs_grid(khcore_ctx *c, int W) { return c->sm_count * max_blocks_per_sm_bfs(W); }
+int bfs_grid(khcore_ctx *c, int W) { return c->sm_count * max_blocks_per_sm_bfs(W, c->block); }
 
 // After a launch that stopped midway (a timed-out barrier) the BFS buffers may
 // hold rows of an unfinished batch: restore the all-zero state.
@@ -399,7 +405,7 @@ khcore_status hdeg_sources(khcore_ctx *c, int W, int32_t h, const int32_t *src, 
         // batches in either layout)
         const int Wb = (W > 1 && cur <= 64) ? 1 : W;
         CU(run_bfs_batch(Wb, g, c->alive, b, src + off, cur, h, c->deg, tune, Wb == W ? grid : bfs_grid(c, Wb),
-                         c->stream, stt ? &stt->kernel_launches : nullptr, c->profiling ? &c->timer : nullptr));
+                         c->block, c->stream, stt ? &stt->kernel_launches : nullptr, c->profiling ? &c->timer : nullptr));
         if (stt) {
             stt->source_batches++;
         }
@@ -674,8 +680,11 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
 // Graph gi of a batch context decomposed alone on the grid-wide path: a
 // context of its own over a copy of its CSR (local ids), the same stream and
 // settings; core indices and rounds go straight into c->core / c->rnd.
-khcore_status decompose_alone(khcore_ctx *c, int32_t gi, int32_t h, khcore_stats *sst)
+// A context of its own over a copy of graph gi's CSR (local ids), on the same
+// stream and with c's settings.
+khcore_status make_sub(khcore_ctx *c, int32_t gi, khcore_ctx **out)
 {
+    *out = nullptr;
     const int64_t v0 = c->v_off[gi];
     const int32_t ng = (int32_t)(c->v_off[gi + 1] - v0);
     std::vector<int32_t> rp((size_t)ng + 1);
@@ -699,8 +708,21 @@ khcore_status decompose_alone(khcore_ctx *c, int32_t gi, int32_t h, khcore_stats
     sub->push_alpha = c->push_alpha;
     sub->lazy = c->lazy;
     sub->update_mode = c->update_mode;
+    sub->block = c->block;
     sub->round_loop = c->round_loop;
     sub->wait_limit_ns = c->wait_limit_ns;
+    *out = sub;
+    return KHCORE_OK;
+}
+
+// Graph gi of a batch context decomposed alone on the grid-wide path;
+// core indices and rounds go straight into c->core / c->rnd.
+khcore_status decompose_alone(khcore_ctx *c, int32_t gi, int32_t h, khcore_stats *sst)
+{
+    khcore_ctx *sub = nullptr;
+    khcore_status s = make_sub(c, gi, &sub);
+    if (s != KHCORE_OK) return s;
+    const int64_t v0 = c->v_off[gi];
     s = decompose(sub, std::vector<int32_t>{h}, c->core + v0, c->rnd + v0, sst);
     if (s != KHCORE_OK) {
         const std::string msg = sub->err;
@@ -827,7 +849,7 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
     if (all_blocks || (c->graph_blocks == 0 && G >= 2)) {
         std::vector<int32_t> small, large;
         for (int32_t gi = 0; gi < G; gi++)
-            (all_blocks || c->v_off[gi + 1] - c->v_off[gi] <= kBlockGraphsMaxN ? small : large).push_back(gi);
+            (all_blocks || c->v_off[gi + 1] - c->v_off[gi] <= c->block_graph_max ? small : large).push_back(gi);
         std::stable_sort(small.begin(), small.end(), [&](int32_t x, int32_t y) {
             return c->v_off[x + 1] - c->v_off[x] > c->v_off[y + 1] - c->v_off[y];
         });
@@ -1234,7 +1256,7 @@ void khcore_destroy(khcore_ctx *c)
                     c->Fx, c->flagx, c->tflag, c->flag[0], c->flag[1], c->Q[0], c->Q[1], c->Q[2], c->I[0], c->I[1], c->I[2], c->T, c->ctl,
                     c->cnt, c->edges, c->alg};
     for (void *p : bufs) cudaFree(p);
-    void *sbufs[] = {c->s_in, c->s_sel0, c->s_sel, c->s_d0, c->s_full};
+    void *sbufs[] = {c->s_in, c->s_sel0, c->s_sel, c->s_d0, c->s_full, c->class_counts};
     for (void *p : sbufs) cudaFree(p);
     void *ubufs[] = {c->upd.vis, c->upd.list, c->upd.dist, c->upd.reach, c->upd.meta, c->upd.owner, c->upd.lab,
                      c->upd.done, c->upd.flag, c->upd.cand[0], c->upd.cand[1]};
@@ -1355,6 +1377,245 @@ khcore_status khcore_set_lazy(khcore_ctx *c, int32_t on)
 {
     if (!c) return KHCORE_EINVAL;
     c->lazy = on != 0;
+    return KHCORE_OK;
+}
+
+khcore_status khcore_set_degree_classes(khcore_ctx *c, int32_t light_max, int32_t medium_max)
+{
+    khcore_status s;
+    if ((s = check_ctx(c)) != KHCORE_OK) return s;
+    if (light_max < 0 || medium_max < light_max)
+        return fail(c, KHCORE_EINVAL, "degree classes need 0 <= light_max <= medium_max (got %d, %d)", light_max,
+                    medium_max);
+    if (!c->class_counts) CU(dev_alloc(&c->class_counts, 6));
+    int32_t cnt[3] = {0, 0, 0};
+    CU(launch_degree_classes(c->row_ptr, c->n, light_max, medium_max, c->classes, c->class_counts, c->stream));
+    CU(cudaMemcpyAsync(cnt, c->class_counts, sizeof cnt, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    c->n_light = cnt[0];
+    c->n_medium = cnt[1];
+    c->n_heavy = cnt[2];
+    c->light_max = light_max;
+    c->medium_max = medium_max;
+    return KHCORE_OK;
+}
+
+khcore_status khcore_set_block_size(khcore_ctx *c, int32_t threads)
+{
+    if (!c || (threads != 128 && threads != 256 && threads != 512)) return KHCORE_EINVAL;
+    c->block = threads;
+    return KHCORE_OK;
+}
+
+khcore_status khcore_set_block_graph_max(khcore_ctx *c, int32_t nmax)
+{
+    if (!c || nmax < 0) return KHCORE_EINVAL;
+    c->block_graph_max = nmax;
+    return KHCORE_OK;
+}
+
+namespace {
+
+// One line of the tuning cache: {"key": "...", "words": W, ...}.
+bool cache_lookup(const char *path, const std::string &key, khcore_tuning *t)
+{
+    FILE *f = path ? fopen(path, "r") : nullptr;
+    if (!f) return false;
+    char line[1024];
+    bool found = false;
+    const std::string want = "\"key\": \"" + key + "\"";
+    while (fgets(line, sizeof line, f)) {
+        if (!strstr(line, want.c_str())) continue;
+        khcore_tuning r;
+        std::memset(&r, 0, sizeof r);
+        auto num = [&](const char *name, int32_t *dst) {
+            const std::string tag = std::string("\"") + name + "\": ";
+            const char *p = strstr(line, tag.c_str());
+            return p && sscanf(p + tag.size(), "%d", dst) == 1;
+        };
+        if (num("words", &r.words) && num("block", &r.block) && num("light_max", &r.light_max) &&
+            num("medium_max", &r.medium_max) && num("push_alpha", &r.push_alpha) &&
+            num("block_graph_max", &r.block_graph_max)) {
+            *t = r;  // the last matching line wins
+            found = true;
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+void cache_store(const char *path, const std::string &key, const khcore_tuning &t)
+{
+    FILE *f = path ? fopen(path, "a") : nullptr;
+    if (!f) return;
+    fprintf(f,
+            "{\"key\": \"%s\", \"words\": %d, \"block\": %d, \"light_max\": %d, \"medium_max\": %d, "
+            "\"push_alpha\": %d, \"block_graph_max\": %d, \"trial_ms\": %.3f}\n",
+            key.c_str(), t.words, t.block, t.light_max, t.medium_max, t.push_alpha, t.block_graph_max, t.trial_ms);
+    fclose(f);
+}
+
+int ilog2(int64_t x)
+{
+    int l = 0;
+    while (x > 1) {
+        x >>= 1;
+        l++;
+    }
+    return l;
+}
+
+}  // namespace
+
+khcore_status khcore_autotune(khcore_ctx *c, int32_t h, const char *cache_path, khcore_tuning *out)
+{
+    khcore_status s;
+    if ((s = check_ctx(c)) != KHCORE_OK) return s;
+    if (h < 1) return fail(c, KHCORE_EINVAL, "h must be >= 1 (got %d)", h);
+    khcore_tuning t;
+    std::memset(&t, 0, sizeof t);
+    t.words = c->W_req ? c->W_req : auto_words(c->n);
+    t.block = c->block;
+    t.light_max = c->light_max;
+    t.medium_max = c->medium_max;
+    t.push_alpha = c->push_alpha;
+    t.block_graph_max = c->block_graph_max;
+    if (c->n == 0) {
+        if (out) *out = t;
+        return KHCORE_OK;
+    }
+    // cache key: the GPU, the graph's size classes and h
+    cudaDeviceProp prop;
+    CU(cudaGetDeviceProperties(&prop, c->device));
+    std::vector<int32_t> rp;
+    CU(fetch(rp, c->row_ptr, (size_t)c->n + 1));
+    int64_t dmax = 0;
+    for (int32_t v = 0; v < c->n; v++) dmax = std::max<int64_t>(dmax, rp[v + 1] - rp[v]);
+    const int32_t he = effective_h(c->n, h);
+    char kb[512];
+    snprintf(kb, sizeof kb, "%s|G:%d|n:2^%d|m:2^%d|dmax:2^%d|h:%d", prop.name, c->G, ilog2(c->n), ilog2(c->m + 1),
+             ilog2(dmax + 1), he);
+    const std::string key = kb;
+    khcore_tuning cached;
+    if (cache_lookup(cache_path, key, &cached)) {
+        t = cached;
+        t.from_cache = 1;
+    } else if (c->G == 1) {
+        // The all-vertex pass decides the one-graph knobs: time it on the
+        // first S vertices as sources (4 batches of the widest W), knob by
+        // knob, keeping the best value of each before tuning the next. The
+        // h-degrees of every trial must agree (results do not depend on the
+        // knobs).
+        const int32_t S = std::min<int32_t>(c->n, 4096);
+        if ((s = ensure_bfs(c, 16)) != KHCORE_OK) return s;
+        if ((s = clear_if_dirty(c)) != KHCORE_OK) return s;
+        CU(launch_alive_init(c->alive, c->n, c->stream));
+        CU(launch_iota(c->comb, S, c->stream));
+        std::vector<int32_t> ref, got;
+        cudaEvent_t e0, e1;
+        CU(cudaEventCreate(&e0));
+        CU(cudaEventCreate(&e1));
+        auto trial = [&](const khcore_tuning &k, float *ms) -> khcore_status {
+            khcore_status st;
+            if ((st = khcore_set_degree_classes(c, k.light_max, k.medium_max)) != KHCORE_OK) return st;
+            c->block = k.block;
+            c->push_alpha = k.push_alpha;
+            float best = 1e30f;
+            for (int rep = 0; rep < 2; rep++) {
+                CU(cudaEventRecord(e0, c->stream));
+                if ((st = hdeg_sources(c, k.words, he, c->comb, S, c->n, c->m, nullptr)) != KHCORE_OK) return st;
+                CU(cudaEventRecord(e1, c->stream));
+                CU(cudaEventSynchronize(e1));
+                float m = 0.f;
+                CU(cudaEventElapsedTime(&m, e0, e1));
+                best = std::min(best, m);
+            }
+            got.resize(S);
+            CU(cudaMemcpy(got.data(), c->deg, sizeof(int32_t) * S, cudaMemcpyDeviceToHost));
+            if (ref.empty()) ref = got;
+            else if (got != ref) return fail(c, KHCORE_EINTERNAL, "autotune: h-degrees differ between settings");
+            *ms = best;
+            t.trials++;
+            t.trial_ms += best;
+            return KHCORE_OK;
+        };
+        const int32_t cand_words[] = {4, 8, 16}, cand_block[] = {128, 256, 512};
+        const int32_t cand_light[] = {16, 32, 64}, cand_medium[] = {256, 1024, 4096}, cand_alpha[] = {4, 16, 64};
+        struct Knob {
+            int32_t khcore_tuning::*field;
+            const int32_t *cand;
+            int count;
+        } knobs[] = {{&khcore_tuning::words, cand_words, 3},       {&khcore_tuning::block, cand_block, 3},
+                     {&khcore_tuning::light_max, cand_light, 3},   {&khcore_tuning::medium_max, cand_medium, 3},
+                     {&khcore_tuning::push_alpha, cand_alpha, 3}};
+        khcore_status st = KHCORE_OK;
+        for (const Knob &kn : knobs) {
+            int32_t best_v = t.*kn.field;
+            float best_ms = 1e30f;
+            for (int i = 0; i < kn.count && st == KHCORE_OK; i++) {
+                khcore_tuning k = t;
+                k.*kn.field = kn.cand[i];
+                if (k.light_max > k.medium_max) continue;
+                float ms = 0.f;
+                if ((st = trial(k, &ms)) == KHCORE_OK && ms < best_ms) {
+                    best_ms = ms;
+                    best_v = kn.cand[i];
+                }
+            }
+            t.*kn.field = best_v;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (st != KHCORE_OK) return st;
+        cache_store(cache_path, key, t);
+    } else {
+        // Batches: the largest graph size that one thread block decomposes
+        // faster than the whole grid, from up to 8 graphs of 512 to 32768
+        // vertices timed both ways (each alone in a context of its own)
+        std::vector<int32_t> mid;
+        for (int32_t gi = 0; gi < c->G; gi++) {
+            const int64_t ng = c->v_off[gi + 1] - c->v_off[gi];
+            if (ng >= 512 && ng <= 32768) mid.push_back(gi);
+        }
+        std::sort(mid.begin(), mid.end(), [&](int32_t a, int32_t b) {
+            return c->v_off[a + 1] - c->v_off[a] < c->v_off[b + 1] - c->v_off[b];
+        });
+        std::vector<int32_t> pick;
+        for (int i = 0; i < 8 && !mid.empty(); i++) pick.push_back(mid[(size_t)i * (mid.size() - 1) / 7]);
+        pick.erase(std::unique(pick.begin(), pick.end()), pick.end());
+        int32_t cut = 0;
+        for (int32_t gi : pick) {
+            double ms[2] = {0, 0};
+            for (int mode = 0; mode < 2; mode++) {
+                khcore_ctx *sub = nullptr;
+                if ((s = make_sub(c, gi, &sub)) != KHCORE_OK) return s;
+                sub->graph_blocks = mode == 0 ? 1 : 0;  // 1: one thread block; 0: the grid-wide path
+                khcore_stats st;
+                for (int rep = 0; rep < 2 && s == KHCORE_OK; rep++)
+                    s = decompose(sub, std::vector<int32_t>{h}, nullptr, nullptr, &st);
+                if (s != KHCORE_OK) {
+                    const std::string msg = sub->err;
+                    khcore_destroy(sub);
+                    return fail(c, s, "autotune, graph %d: %s", gi, msg.c_str());
+                }
+                ms[mode] = st.device_ms;
+                t.trials++;
+                t.trial_ms += st.device_ms;
+                khcore_destroy(sub);
+            }
+            const int32_t ng = (int32_t)(c->v_off[gi + 1] - c->v_off[gi]);
+            if (ms[0] <= ms[1]) cut = std::max(cut, ng);
+        }
+        if (!pick.empty()) t.block_graph_max = cut;
+        cache_store(cache_path, key, t);
+    }
+    // apply
+    if ((s = khcore_set_degree_classes(c, t.light_max, t.medium_max)) != KHCORE_OK) return s;
+    c->W_req = t.words;
+    c->block = t.block;
+    c->push_alpha = t.push_alpha;
+    c->block_graph_max = t.block_graph_max;
+    if (out) *out = t;
     return KHCORE_OK;
 }
 

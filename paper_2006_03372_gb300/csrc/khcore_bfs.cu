@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(kBlock) k_weight_pass(BfsBufs b, const int32_t
 
 template <int W>
 cudaError_t bfs_batch_t(const GraphView &g, const uint32_t *alive, const BfsBufs &b, const int32_t *src,
-                        int32_t ns, int32_t h, int32_t *deg, BfsTuning tune, int grid, cudaStream_t s,
+                        int32_t ns, int32_t h, int32_t *deg, BfsTuning tune, int grid, int block, cudaStream_t s,
                         int64_t *launches, LevelTimer *timer)
 {
     const int tb = ((ns + 31) / 32) * 32;
@@ -51,24 +51,24 @@ cudaError_t bfs_batch_t(const GraphView &g, const uint32_t *alive, const BfsBufs
         const bool timed = timer && timer->used < timer->cap;
         if (timed) cudaEventRecord(timer->ev[2 * timer->used], s);
         if (lvl == h - 1)
-            k_level<W, true><<<grid, kBlock, 0, s>>>(g, alive, b, lvl, tune);
+            k_level<W, true><<<grid, block, 0, s>>>(g, alive, b, lvl, tune);
         else
-            k_level<W, false><<<grid, kBlock, 0, s>>>(g, alive, b, lvl, tune);
+            k_level<W, false><<<grid, block, 0, s>>>(g, alive, b, lvl, tune);
         if (timed) {
             cudaEventRecord(timer->ev[2 * timer->used + 1], s);
             timer->used++;
         }
         if (lvl == h - 1)
-            k_post<W, true><<<grid, kBlock, 0, s>>>(g, b, lvl, tune);
+            k_post<W, true><<<grid, block, 0, s>>>(g, b, lvl, tune);
         else
-            k_post<W, false><<<grid, kBlock, 0, s>>>(g, b, lvl, tune);
+            k_post<W, false><<<grid, block, 0, s>>>(g, b, lvl, tune);
         l += 2;
         if (b.wsum && (lvl == h - 2 || lvl == h - 3)) {
-            k_weight_pass<W><<<grid, kBlock, 0, s>>>(b, src, g.row_ptr, alive, lvl == h - 2);
+            k_weight_pass<W><<<grid, block, 0, s>>>(b, src, g.row_ptr, alive, lvl == h - 2);
             l++;
         }
     }
-    k_end<W><<<grid, kBlock, 0, s>>>(b, src, ns, deg);
+    k_end<W><<<grid, block, 0, s>>>(b, src, ns, deg);
     l++;
     if (launches) *launches += l;
     return cudaGetLastError();
@@ -77,31 +77,31 @@ cudaError_t bfs_batch_t(const GraphView &g, const uint32_t *alive, const BfsBufs
 }  // namespace
 
 cudaError_t run_bfs_batch(int W, const GraphView &g, const uint32_t *alive, const BfsBufs &b, const int32_t *src,
-                          int32_t ns, int32_t h, int32_t *deg, BfsTuning tune, int grid, cudaStream_t s,
+                          int32_t ns, int32_t h, int32_t *deg, BfsTuning tune, int grid, int block, cudaStream_t s,
                           int64_t *launches, LevelTimer *timer)
 {
     if (ns <= 0) return cudaSuccess;
-    if (ns > 64 * W) return cudaErrorInvalidValue;
+    if (ns > 64 * W || block < 64 || block > kBlock || block % 32) return cudaErrorInvalidValue;
     switch (W) {
-    case 1: return bfs_batch_t<1>(g, alive, b, src, ns, h, deg, tune, grid, s, launches, timer);
-    case 2: return bfs_batch_t<2>(g, alive, b, src, ns, h, deg, tune, grid, s, launches, timer);
-    case 4: return bfs_batch_t<4>(g, alive, b, src, ns, h, deg, tune, grid, s, launches, timer);
-    case 8: return bfs_batch_t<8>(g, alive, b, src, ns, h, deg, tune, grid, s, launches, timer);
-    case 16: return bfs_batch_t<16>(g, alive, b, src, ns, h, deg, tune, grid, s, launches, timer);
+    case 1: return bfs_batch_t<1>(g, alive, b, src, ns, h, deg, tune, grid, block, s, launches, timer);
+    case 2: return bfs_batch_t<2>(g, alive, b, src, ns, h, deg, tune, grid, block, s, launches, timer);
+    case 4: return bfs_batch_t<4>(g, alive, b, src, ns, h, deg, tune, grid, block, s, launches, timer);
+    case 8: return bfs_batch_t<8>(g, alive, b, src, ns, h, deg, tune, grid, block, s, launches, timer);
+    case 16: return bfs_batch_t<16>(g, alive, b, src, ns, h, deg, tune, grid, block, s, launches, timer);
     default: return cudaErrorInvalidValue;
     }
 }
 
-int max_blocks_per_sm_bfs(int W)
+int max_blocks_per_sm_bfs(int W, int block)
 {
     int nb = 1;
     cudaError_t e = cudaSuccess;
     switch (W) {
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_level<1, false>, kBlock, 0); break;
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_level<2, false>, kBlock, 0); break;
-    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_level<4, false>, kBlock, 0); break;
-    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_level<8, false>, kBlock, 0); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_level<16, false>, kBlock, 0); break;
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_level<1, false>, block, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_level<2, false>, block, 0); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_level<4, false>, block, 0); break;
+    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_level<8, false>, block, 0); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_level<16, false>, block, 0); break;
     }
     if (e != cudaSuccess || nb < 1) nb = 1;
     return nb;

@@ -173,6 +173,8 @@ struct Acc {
     unsigned long long scanned;  // plain-BFS-equivalent CSR entries
     unsigned long long fe;       // degree sum of vertices appended to the next frontier
     unsigned long long newv;     // vertices first reached at the last level (when b.newcnt is set)
+    unsigned long long gathered; // pull: frontier rows OR-ed in (one per flagged CSR entry)
+    unsigned long long rows;     // pull: vertices with a frontier neighbour (own rows read / written)
 };
 
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
@@ -243,7 +245,8 @@ __device__ __forceinline__ void or_row(uint64_t (&a)[W], const uint64_t *F, int3
 template <int W>
 __device__ __forceinline__ void gather_edges(uint64_t (&a)[W], const int32_t *col,
                                              const uint32_t *flc, const uint64_t *Fc,
-                                             int32_t first, int32_t e1, int32_t stride)
+                                             int32_t first, int32_t e1, int32_t stride,
+                                             unsigned long long &gathered)
 {
     int32_t e = first;
     for (; e + stride < e1; e += 2 * stride) {
@@ -253,10 +256,14 @@ __device__ __forceinline__ void gather_edges(uint64_t (&a)[W], const int32_t *co
         const bool f1 = flag_test(flc, x1);
         if (f0) or_row<W>(a, Fc, x0);
         if (f1) or_row<W>(a, Fc, x1);
+        gathered += (unsigned)f0 + (unsigned)f1;
     }
     if (e < e1) {
         const int32_t x0 = __ldg(&col[e]);
-        if (flag_test(flc, x0)) or_row<W>(a, Fc, x0);
+        if (flag_test(flc, x0)) {
+            or_row<W>(a, Fc, x0);
+            gathered++;
+        }
     }
 }
 
@@ -315,7 +322,7 @@ __device__ __forceinline__ void dev_seed(const int32_t *src, int32_t ns, BfsBufs
         if (b.in_s && b.sel0 && b.sel0[s] == 0)
             atomicOr(reinterpret_cast<unsigned long long *>(&b.fullmask[word]), (unsigned long long)bit);
     }
-    Acc dummy{0, 0, 0};
+    Acc dummy{0, 0, 0, 0, 0};
     append_frontier<W>(i < ns, s, (int32_t)d, b, 0, dummy, rp);  // Q[0] and the level-0 push items
     const unsigned long long ws = warp_sum(d);
     if ((i & 31) == 0 && ws) atomicAdd(&s_fe, ws);
@@ -382,15 +389,28 @@ __device__ __forceinline__ void pull_groups(const int32_t *list, int32_t count, 
                 act = true;
                 const int32_t e0 = rp[y], e1 = rp[y + 1];
                 dy = e1 - e0;
-                gather_edges<W>(a, g.col, flc, Fc, e0 + gi, e1, G);
+                gather_edges<W>(a, g.col, flc, Fc, e0 + gi, e1, G, acc.gathered);
             }
         }
+        // no frontier neighbour for any vertex of this warp (most warps at the
+        // last level): nothing to combine, count or store
+        bool mine = false;
+#pragma unroll
+        for (int k = 0; k < W; k++) mine |= a[k] != 0;
+        if (!__any_sync(kFull, mine)) continue;  // warp-uniform
         group_or<W, G>(a);
+        // a vertex none of whose neighbours is in the frontier has nothing to
+        // do: its own rows are not touched (most vertices at the last level);
+        // a is the same on every lane of the group here
+        bool any_a = false;
+#pragma unroll
+        for (int k = 0; k < W; k++) any_a |= a[k] != 0;
         uint64_t nw = 0, v = 0;
-        if (act && gi < W) {
+        if (act && any_a && gi < W) {
             v = V[(size_t)y * W + gi];
             nw = select_word<W>(a, gi) & ~v;
         }
+        if (act && any_a && gi == 0) acc.rows++;
         swar_step<W>(sw, nw & elig_mask(b, gi, act ? y : -1), cnt_s);
         if (b.rowcnt) {  // uniform
             int32_t rc = __popcll(nw & row_mask(gi, b.row_first));
@@ -471,8 +491,11 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
     if (FUSED && lvl > 0) clear_slot<W>(b, (lvl + 2) % 3);
     for (int i = threadIdx.x; i < 64 * W; i += blockDim.x) cnt_s[i] = 0;
     // Algorithmic bytes of this level. Pull: 4 n_b (row offsets) + 4 m_b
-    // (column ids) + 16 W n_b (own visited and next-frontier rows) over the
-    // n_b alive rows and their m_b entries. Push: the frontier rows it reads
+    // (column ids) over the n_b alive rows and their m_b entries, 8 W per
+    // frontier entry gathered (the neighbour's frontier row), and 16 W per
+    // vertex with a frontier neighbour (its visited row read, its
+    // next-frontier row written), the last two counted as the level runs.
+    // Push: the frontier rows it reads
     // (8 W per frontier vertex) and, per frontier entry, the column id, the
     // neighbour's visited row and its next-frontier row (4 + 16 W).
     if (blockIdx.x == 0 && threadIdx.x == 0 && b.alg_bytes) {
@@ -480,7 +503,7 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
         const unsigned long long bytes =
             push ? (unsigned long long)b.ctl->fe[cslot] * (4ull + 16ull * W) +
                        (unsigned long long)b.ctl->q[cslot] * 8ull * W
-                 : 4ull * nb + 4ull * tune.m_alive + 16ull * W * nb;
+                 : 4ull * nb + 4ull * tune.m_alive;
         atomicAdd(b.alg_bytes, bytes);
     }
     __syncthreads();
@@ -493,7 +516,7 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
     const int32_t *col = g.col;
     Swar sw;
     sw.reset();
-    Acc acc{0, 0, 0};
+    Acc acc{0, 0, 0, 0, 0};
 
     if (push) {
         // ---------------- push: frontier vertices scatter to neighbours ----
@@ -588,7 +611,8 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
                     uint64_t a[W];
 #pragma unroll
                     for (int k = 0; k < W; k++) a[k] = 0;
-                    gather_edges<W>(a, col, flc, Fc, e0 + (int32_t)threadIdx.x, e1, (int32_t)blockDim.x);
+                    gather_edges<W>(a, col, flc, Fc, e0 + (int32_t)threadIdx.x, e1, (int32_t)blockDim.x,
+                                    acc.gathered);
                     group_or<W, 32>(a);
                     if (lane < W) red[wid][lane] = select_word<W>(a, lane);
                 }
@@ -601,6 +625,7 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
                         v = V[(size_t)y * W + j];
                         nw = m & ~v;
                     }
+                    if (act && lane == 0) acc.rows++;
                     swar_step<W>(sw, nw & elig_mask(b, lane, act ? y : -1), cnt_s);
                     if (b.rowcnt) {
                         int32_t rc = __popcll(nw & row_mask(lane, b.row_first));
@@ -623,10 +648,12 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
     const unsigned long long sc = warp_sum(acc.scanned);
     const unsigned long long fe = warp_sum(acc.fe);
     const unsigned long long nv = warp_sum(acc.newv);
+    const unsigned long long gb = warp_sum(8ull * W * (acc.gathered + 2ull * acc.rows));
     if (lane == 0) {
         if (sc) atomicAdd(b.edges, sc);
         if (fe) atomicAdd(&b.ctl->fe[nslot], fe);
         if (nv) atomicAdd(b.newcnt, nv);
+        if (gb && b.alg_bytes) atomicAdd(b.alg_bytes, gb);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < 64 * W; i += blockDim.x) {

@@ -186,9 +186,11 @@ cudaError_t launch_alive_init(uint32_t *alive, int32_t n, cudaStream_t s);
 // grid = number of blocks for the level kernels.
 // timer (nullable): an event pair is recorded around each level launch
 // while pairs are left in the pool.
+// block: threads per block of the batch's kernels (a multiple of 32, at
+// most kBlock).
 cudaError_t run_bfs_batch(int W, const GraphView &g, const uint32_t *alive, const BfsBufs &b,
                           const int32_t *src, int32_t ns, int32_t h, int32_t *deg, BfsTuning tune,
-                          int grid, cudaStream_t s, int64_t *launches, LevelTimer *timer);
+                          int grid, int block, cudaStream_t s, int64_t *launches, LevelTimer *timer);
 
 // Peel round pieces (khcore_peel.cu).
 cudaError_t launch_min_alive_deg(const GraphView &g, const uint32_t *alive, const int32_t *deg, const PeelView &p,
@@ -231,7 +233,13 @@ cudaError_t launch_sum_classes(const PeelView &p, PeelState *st, cudaStream_t s)
 // h is lvl + 1 (the vertices found so far are those closer than h).
 cudaError_t launch_snapshot_inner(const PeelView &p, const int32_t *cls_h, int lvl, int32_t *inner, cudaStream_t s);
 
-int max_blocks_per_sm_bfs(int W);
+int max_blocks_per_sm_bfs(int W, int block = kBlock);
+
+// Degree classes of the pull direction: classes = the vertices with
+// deg <= light_max, then those with deg <= medium_max, then the rest;
+// counts[0..2] receives the class sizes (device pointers; counts zeroed here).
+cudaError_t launch_degree_classes(const int32_t *rp, int32_t n, int32_t light_max, int32_t medium_max,
+                                  int32_t *classes, int32_t *counts, cudaStream_t s);
 
 // ---- the paper's exact update after one deletion (khcore_update.cu) ---------
 // Slots of the per-deleted-vertex update (Algorithm 3 with Algorithm 4's

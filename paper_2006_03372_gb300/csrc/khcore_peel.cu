@@ -56,6 +56,25 @@ __global__ void k_concat(int32_t *dst, const int32_t *a, int32_t na, const int32
 {
     dev_concat(dst, a, na, b, nb);
 }
+__global__ void k_class_count(const int32_t *rp, int32_t n, int32_t l, int32_t m, int32_t *counts)
+{
+    int32_t c[3] = {0, 0, 0};
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t d = rp[v + 1] - rp[v];
+        c[d <= l ? 0 : (d <= m ? 1 : 2)]++;
+    }
+    for (int k = 0; k < 3; k++)
+        if (c[k]) atomicAdd(&counts[k], c[k]);
+}
+__global__ void k_class_fill(const int32_t *rp, int32_t n, int32_t l, int32_t m, int32_t *counts, int32_t *classes)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t d = rp[v + 1] - rp[v];
+        const int k = d <= l ? 0 : (d <= m ? 1 : 2);
+        const int32_t base = k == 0 ? 0 : (k == 1 ? counts[0] : counts[0] + counts[1]);
+        classes[base + atomicAdd(&counts[3 + k], 1)] = (int32_t)v;
+    }
+}
 // Sampling variant: the running select count starts at select0, or at the
 // exact h-degree for a vertex without a rate (select0 = 0).
 __global__ void k_sample_init(const int32_t *sel0, const int32_t *d0, int32_t *sel, int32_t n)
@@ -173,6 +192,17 @@ cudaError_t launch_sample_init(const int32_t *sel0, const int32_t *d0, int32_t *
 {
     if (n <= 0) return cudaSuccess;
     k_sample_init<<<(n + 255) / 256 < 2048 ? (n + 255) / 256 : 2048, 256, 0, s>>>(sel0, d0, sel, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_degree_classes(const int32_t *rp, int32_t n, int32_t light_max, int32_t medium_max,
+                                  int32_t *classes, int32_t *counts, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(counts, 0, 6 * sizeof(int32_t), s);
+    if (e != cudaSuccess || n <= 0) return e;
+    const int blocks = (n + 255) / 256 < 2048 ? (n + 255) / 256 : 2048;
+    k_class_count<<<blocks, 256, 0, s>>>(rp, n, light_max, medium_max, counts);
+    k_class_fill<<<blocks, 256, 0, s>>>(rp, n, light_max, medium_max, counts, classes);
     return cudaGetLastError();
 }
 

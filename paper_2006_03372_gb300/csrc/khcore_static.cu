@@ -272,7 +272,7 @@ extern "C" khcore_status khcore_hdegrees_static(int32_t n, int64_t m, const int3
     int32_t *deg = (int32_t *)(base + L.deg);
     constexpr int32_t S = 64 * kStaticW;
     for (int32_t off = 0; off < count; off += S)
-        SCU(run_bfs_batch(kStaticW, g, alive, b, verts + off, std::min(S, count - off), hh, deg, tune, slot.grid, s,
+        SCU(run_bfs_batch(kStaticW, g, alive, b, verts + off, std::min(S, count - off), hh, deg, tune, slot.grid, kBlock, s,
                           nullptr, nullptr));
     k_static_gather<<<(count + kBlock - 1) / kBlock, kBlock, 0, s>>>(verts, count, deg, deg_out);
     SCU(cudaGetLastError());
