@@ -45,7 +45,11 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--graph", default="cl1m", help="graphgen.CONFIGS key")
     p.add_argument("--hs", default="2", help="comma-separated h values decomposed per step")
-    p.add_argument("--words", type=int, default=0, help="64-bit source words per vertex (0 = auto)")
+    p.add_argument("--words", type=int, default=0, help="64-bit source words per vertex (0 = autotuned)")
+    p.add_argument("--no-autotune", action="store_true", help="keep the default knobs instead of khcore_autotune")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the once-per-run decompositions of the other configurations (Chung-Lu h=3, "
+                        "R-MAT h=4 and h=5)")
     p.add_argument("--e2e-steps", type=int, default=1, help="end-to-end runs through host buffers (0: skip)")
     p.add_argument("--ref-removals", type=int, default=256,
                    help="reference arm: Algorithm 1 removals timed per step after the full h-degree pass")
@@ -136,7 +140,7 @@ def workload_name(args, g) -> str:
 # `python bench.py --steps 1 --warmup 0 --no-cpu-baseline --e2e-steps 0`
 # (the ncu capture of this kernel), keyed by a digest of the kernel sources it
 # was taken on: reported only while the sources are unchanged.
-KERNEL_TRAFFIC = {("cl1m", (2,), "82959768d651a8c2"): 50.12e9}
+KERNEL_TRAFFIC = {("cl1m", (2,), "5d3f65f6632538e4"): 15311525120 + 3119099136}
 
 
 def kernel_source_digest() -> str:
@@ -305,6 +309,11 @@ def run_ours(args):
     rp_d = torch.from_numpy(g.row_ptr).cuda()
     col_d = torch.from_numpy(g.col).cuda()
     ctx = kh.khcore_create(g.n, rp_d, col_d, kh.FLAG_TRUST_INPUT, stream)
+    import tempfile
+    tune_cache = os.path.join(tempfile.gettempdir(), f"khcore_tune_{os.getpid()}.jsonl")
+    tuning = None
+    if not args.no_autotune and not args.words:
+        tuning = kh.khcore_autotune(ctx, hs[0], tune_cache)  # outside the timed region
     if args.words:
         kh.khcore_set_words(ctx, args.words)
     kh.khcore_set_profiling(ctx, 1)
@@ -371,6 +380,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         c2 = kh.khcore_create(g.n, rp_h, col_h, kh.FLAG_TRUST_INPUT, stream)
+        if tuning is not None:
+            kh.khcore_autotune(c2, hs[0], tune_cache)  # a user's call: the cached choice, no measuring
         if args.words:
             kh.khcore_set_words(c2, args.words)
         for h in hs:
@@ -400,13 +411,34 @@ def run_ours(args):
                                  if rnd_ms >= lvl_ms else None),
                      "kernel": kname, "time_share": kshare, "peak_kind": peak_kind},
         "phase_ms": {"initial_pass": sum(s["init_ms"] for s in stats) / args.steps,
-                     "rounds": rnd_ms / args.steps},
+                     "rounds": rnd_ms / args.steps,
+                     "round_phases": dict(zip(["level", "refine", "peel_set", "affected_bfs", "update"],
+                                              [x for x in stats[-1]["phase_ms"]]))},
+        "grid_barriers_per_round": {str(h): st_last[h]["grid_barriers"] / max(1, st_last[h]["rounds"]) for h in hs},
+        "tuning": tuning,
         "clocks": clk,
         "e2e": {"value": world * len(hs) / e2e_s if e2e_times else None, "unit": UNIT,
                 "h2d_bytes_per_step": int(4 * (g.n + 1 + g.m_directed)),
                 "d2h_bytes_per_step": int(4 * g.n * len(hs))},
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
     }
+    if rank == 0 and world == 1 and not args.no_extras and args.graph == "cl1m":
+        # the other configurations' decompositions, once each (device time by
+        # CUDA events, clocks sampled meanwhile): not part of value
+        extras = {}
+        clk2 = ClockSampler(local)
+        clk2.start()
+        for name, h in (("rmat18", 4), ("rmat18", 5), ("cl1m", 3)):
+            gx = g if name == "cl1m" else gg.config_graph(name)
+            with kh.KHCore.from_graph(gx, flags=kh.FLAG_TRUST_INPUT) as cx:
+                if tuning is not None:
+                    kh.khcore_autotune(cx.ctx, h, tune_cache)
+                _, _, sx = cx.decompose_ex(h)
+            extras[f"{name}_h{h}"] = {"workload": workload_name(argparse.Namespace(graph=name), gx) if name != "cl1m"
+                                      else WORKLOAD, "decompose_ms": sx["device_ms"], "rounds": sx["rounds"],
+                                      "initial_pass_ms": sx["init_ms"], "rounds_ms": sx["round_ms"]}
+        extras["clocks"] = clk2.stop()
+        line["extra_configs"] = extras
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(g, hs, args.ref_removals)
         # the measured pair on the one configuration the oracle finishes in
@@ -444,6 +476,11 @@ def run_hdeg(args):
     rp_d = torch.from_numpy(g.row_ptr).cuda()
     col_d = torch.from_numpy(g.col).cuda()
     ctx = kh.khcore_create(g.n, rp_d, col_d, kh.FLAG_TRUST_INPUT, stream)
+    import tempfile
+    tune_cache = os.path.join(tempfile.gettempdir(), f"khcore_tune_{os.getpid()}.jsonl")
+    tuning = None
+    if not args.no_autotune and not args.words:
+        tuning = kh.khcore_autotune(ctx, hs[0], tune_cache)  # outside the timed region
     if args.words:
         kh.khcore_set_words(ctx, args.words)
     kh.khcore_set_profiling(ctx, 1)

@@ -353,7 +353,8 @@ typedef struct {
     int32_t block;            /* khcore_set_block_size */
     int32_t light_max;        /* khcore_set_degree_classes */
     int32_t medium_max;
-    int32_t push_alpha;       /* khcore_set_push_alpha */
+    int32_t push_alpha;       /* push alpha of the all-vertex pass only (the rounds
+                                 keep khcore_set_push_alpha's) */
     int32_t block_graph_max;  /* khcore_set_block_graph_max */
     int32_t from_cache;       /* 1: read from the cache file, nothing measured */
     int32_t trials;           /* settings timed */
@@ -366,7 +367,8 @@ typedef struct {
  *   One-graph contexts: the multi-source BFS is timed (CUDA events) on the
  *   first min(n, 4096) vertices as sources, knob by knob (W in {4, 8, 16},
  *   block size in {128, 256, 512}, light_max in {16, 32, 64}, medium_max in
- *   {256, 1024, 4096}, push alpha in {4, 16, 64}), each set to its fastest
+ *   {256, 1024, 4096}, the all-vertex pass's push alpha in {4, 16, 64}),
+ *   each set to its fastest
  *   value before the next is tried; every trial's h-degrees must agree
  *   (KHCORE_EINTERNAL otherwise).
  *   Batch contexts: block_graph_max, from up to 8 graphs of 512 to 32,768

@@ -90,6 +90,7 @@ struct khcore_ctx {
     int32_t medium_max = kMediumMax;
     int32_t block = kBlock;               // threads per block of the per-phase BFS kernels
     int32_t block_graph_max = kBlockGraphsMaxN;  // batches: graphs decomposed by one thread block
+    int32_t init_alpha = 0;               // push alpha of the all-vertex pass (0: push_alpha)
     int32_t *class_counts = nullptr;      // [6] scratch of the class builder
     // the sampling variant (Algorithms 5 and 6): sample bytes, select at the
     // start and now, exact h-degrees at the start, the per-batch mask of the
@@ -349,7 +350,7 @@ khcore_status flush_timer(khcore_ctx *c)
 // sources for the vertices they reach within h-1 (dev_weight_pass).
 khcore_status hdeg_sources(khcore_ctx *c, int W, int32_t h, const int32_t *src, int32_t ns, int64_t n_b,
                            int64_t m_b, khcore_stats *stt, int32_t *rowcnt = nullptr, int32_t row_first = 0,
-                           int32_t *wsum = nullptr)
+                           int32_t *wsum = nullptr, bool all_vertex = false)
 {
     const GraphView g = c->view();
     BfsBufs b;
@@ -388,7 +389,8 @@ khcore_status hdeg_sources(khcore_ctx *c, int W, int32_t h, const int32_t *src, 
     b.sel = c->sampling == 1 ? c->s_sel0 : (c->sampling == 2 ? c->s_sel : nullptr);
     b.d0 = c->sampling == 2 ? c->s_d0 : nullptr;
     BfsTuning tune;
-    tune.alpha = c->push_alpha;
+    // the all-vertex pass may have a push alpha of its own (khcore_autotune)
+    tune.alpha = (all_vertex && c->init_alpha) ? c->init_alpha : c->push_alpha;
     tune.n_alive = (int32_t)n_b;
     tune.m_alive = (unsigned long long)m_b;
     const int32_t S = 64 * W;
@@ -709,6 +711,7 @@ khcore_status make_sub(khcore_ctx *c, int32_t gi, khcore_ctx **out)
     sub->lazy = c->lazy;
     sub->update_mode = c->update_mode;
     sub->block = c->block;
+    sub->init_alpha = c->init_alpha;
     sub->round_loop = c->round_loop;
     sub->wait_limit_ns = c->wait_limit_ns;
     *out = sub;
@@ -929,7 +932,8 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
 
     // initial h-degrees, class by class
     for (int32_t k = 0; k < ncls; k++)
-        if ((s = hdeg_sources(c, W, cls_h[k], c->cls_src + cls_off[k], (int32_t)cls_size[k], c->n, c->m, &stt)) !=
+        if ((s = hdeg_sources(c, W, cls_h[k], c->cls_src + cls_off[k], (int32_t)cls_size[k], c->n, c->m, &stt,
+                              nullptr, 0, nullptr, true)) !=
             KHCORE_OK)
             return s;
 
@@ -943,7 +947,7 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         // h-degrees just computed), then the estimates start at d0
         CU(cudaMemcpyAsync(c->s_d0, c->deg, sizeof(int32_t) * (size_t)c->n, cudaMemcpyDeviceToDevice, c->stream));
         c->sampling = 1;
-        s = hdeg_sources(c, W, cls_h[0], c->cls_src, c->n, c->n, c->m, &stt);
+        s = hdeg_sources(c, W, cls_h[0], c->cls_src, c->n, c->n, c->m, &stt, nullptr, 0, nullptr, true);
         c->sampling = 2;
         if (s != KHCORE_OK) {
             c->sampling = 0;
@@ -1478,7 +1482,7 @@ khcore_status khcore_autotune(khcore_ctx *c, int32_t h, const char *cache_path, 
     t.block = c->block;
     t.light_max = c->light_max;
     t.medium_max = c->medium_max;
-    t.push_alpha = c->push_alpha;
+    t.push_alpha = c->init_alpha ? c->init_alpha : c->push_alpha;
     t.block_graph_max = c->block_graph_max;
     if (c->n == 0) {
         if (out) *out = t;
@@ -1519,11 +1523,13 @@ khcore_status khcore_autotune(khcore_ctx *c, int32_t h, const char *cache_path, 
             khcore_status st;
             if ((st = khcore_set_degree_classes(c, k.light_max, k.medium_max)) != KHCORE_OK) return st;
             c->block = k.block;
-            c->push_alpha = k.push_alpha;
+            c->init_alpha = k.push_alpha;
             float best = 1e30f;
             for (int rep = 0; rep < 2; rep++) {
                 CU(cudaEventRecord(e0, c->stream));
-                if ((st = hdeg_sources(c, k.words, he, c->comb, S, c->n, c->m, nullptr)) != KHCORE_OK) return st;
+                if ((st = hdeg_sources(c, k.words, he, c->comb, S, c->n, c->m, nullptr, nullptr, 0, nullptr, true)) !=
+                    KHCORE_OK)
+                    return st;
                 CU(cudaEventRecord(e1, c->stream));
                 CU(cudaEventSynchronize(e1));
                 float m = 0.f;
@@ -1613,7 +1619,7 @@ khcore_status khcore_autotune(khcore_ctx *c, int32_t h, const char *cache_path, 
     if ((s = khcore_set_degree_classes(c, t.light_max, t.medium_max)) != KHCORE_OK) return s;
     c->W_req = t.words;
     c->block = t.block;
-    c->push_alpha = t.push_alpha;
+    c->init_alpha = t.push_alpha;
     c->block_graph_max = t.block_graph_max;
     if (out) *out = t;
     return KHCORE_OK;
@@ -1737,7 +1743,8 @@ khcore_status khcore_hdegrees_ex(khcore_ctx *c, int32_t h, int32_t *deg_out, khc
     CU(launch_iota(c->src, c->n, c->stream));
     stt.kernel_launches += 2;
     // graphs are disjoint: one BFS over the union gives every graph's h-degrees
-    if ((s = hdeg_sources(c, W, hmax, c->src, c->n, c->n, c->m, &stt)) != KHCORE_OK) return s;
+    if ((s = hdeg_sources(c, W, hmax, c->src, c->n, c->n, c->m, &stt, nullptr, 0, nullptr, true)) != KHCORE_OK)
+        return s;
     CU(cudaEventRecord(c->ev1, c->stream));
     if ((s = write_out(c, deg_out, c->deg)) != KHCORE_OK) return s;
     unsigned long long edges = 0, alg = 0;
@@ -1790,7 +1797,8 @@ khcore_status khcore_hdegrees_of(khcore_ctx *c, int32_t h, int32_t count, const 
     for (int32_t g = 0; g < c->G; g++) hmax = std::max(hmax, effective_h(c->v_off[g + 1] - c->v_off[g], h));
     CU(launch_alive_init(c->alive, c->n, c->stream));
     CU(cudaMemcpyAsync(c->src, vs.data(), sizeof(int32_t) * (size_t)count, cudaMemcpyHostToDevice, c->stream));
-    if ((s = hdeg_sources(c, W, hmax, c->src, count, c->n, c->m, nullptr)) != KHCORE_OK) return s;
+    if ((s = hdeg_sources(c, W, hmax, c->src, count, c->n, c->m, nullptr, nullptr, 0, nullptr, true)) != KHCORE_OK)
+        return s;
     // gather deg[verts[i]] into deg_out[i] on the host side of the copy
     std::vector<int32_t> all((size_t)c->n);
     CU(cudaMemcpyAsync(all.data(), c->deg, sizeof(int32_t) * (size_t)c->n, cudaMemcpyDeviceToHost, c->stream));
