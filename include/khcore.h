@@ -342,6 +342,13 @@ khcore_status khcore_set_degree_classes(khcore_ctx *ctx, int32_t light_max, int3
  * default); EINVAL otherwise. The persistent round kernel keeps 512. */
 khcore_status khcore_set_block_size(khcore_ctx *ctx, int32_t threads);
 
+/* khcore_set_round_blocks — resident 512-thread blocks per SM of the
+ * persistent round kernel when its rows are 4 words wide (the default round
+ * W): 1 (up to 128 registers per thread) or 2 (64); 0 (default) picks 1 for
+ * h <= 2, where the rounds are latency-bound, and 2 for h >= 3. EINVAL
+ * otherwise. */
+khcore_status khcore_set_round_blocks(khcore_ctx *ctx, int32_t blocks);
+
 /* khcore_set_block_graph_max — batch contexts: graphs of at most nmax
  * vertices are decomposed by one thread block each (default 4096; see
  * khcore_set_graph_blocks). EINVAL for nmax < 0. */

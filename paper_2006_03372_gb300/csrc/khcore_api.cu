@@ -91,6 +91,7 @@ struct khcore_ctx {
     int32_t block = kBlock;               // threads per block of the per-phase BFS kernels
     int32_t block_graph_max = kBlockGraphsMaxN;  // batches: graphs decomposed by one thread block
     int32_t init_alpha = 0;               // push alpha of the all-vertex pass (0: push_alpha)
+    int32_t round_blocks = 0;             // round kernel blocks per SM (0: by h)
     int32_t *class_counts = nullptr;      // [6] scratch of the class builder
     // the sampling variant (Algorithms 5 and 6): sample bytes, select at the
     // start and now, exact h-degrees at the start, the per-batch mask of the
@@ -712,6 +713,7 @@ khcore_status make_sub(khcore_ctx *c, int32_t gi, khcore_ctx **out)
     sub->update_mode = c->update_mode;
     sub->block = c->block;
     sub->init_alpha = c->init_alpha;
+    sub->round_blocks = c->round_blocks;
     sub->round_loop = c->round_loop;
     sub->wait_limit_ns = c->wait_limit_ns;
     *out = sub;
@@ -960,8 +962,12 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         khcore_ctx *c;
         ~SamplingOff() { c->sampling = 0; }
     } sampling_off{c};
-    const int pgrid = (c->round_loop == 0 && !paper_update && !sampled) ? c->sm_count * max_blocks_per_sm_persist(Wr)
-                                                                          : 0;
+    // resident blocks per SM of the round kernel (W = 4): one while the
+    // rounds are latency-bound (h <= 2), two for the larger BFS levels of h >= 3
+    const int minb = c->round_blocks ? c->round_blocks : (hmax >= 3 ? 2 : 1);
+    const int pgrid = (c->round_loop == 0 && !paper_update && !sampled)
+                          ? c->sm_count * max_blocks_per_sm_persist(Wr, minb)
+                          : 0;
     if (pgrid > 0) {
         // the whole decomposition in one cooperative launch
         PersistLaunch L;
@@ -1025,7 +1031,7 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         L.timeout_ns = c->wait_limit_ns;
         CU(cudaMemsetAsync(c->gs, 0, sizeof(GridSync), c->stream));
         CU(cudaMemsetAsync(c->pstats, 0, sizeof(PersistStats), c->stream));
-        CU(launch_decompose_persist(Wr, L, pgrid, c->stream));
+        CU(launch_decompose_persist(Wr, L, pgrid, c->stream, minb));
         GridSync gsh;
         PersistStats psh;
         CU(cudaMemcpyAsync(&gsh, c->gs, sizeof gsh, cudaMemcpyDeviceToHost, c->stream));
@@ -1408,6 +1414,13 @@ khcore_status khcore_set_block_size(khcore_ctx *c, int32_t threads)
 {
     if (!c || (threads != 128 && threads != 256 && threads != 512)) return KHCORE_EINVAL;
     c->block = threads;
+    return KHCORE_OK;
+}
+
+khcore_status khcore_set_round_blocks(khcore_ctx *c, int32_t blocks)
+{
+    if (!c || blocks < 0 || blocks > 2) return KHCORE_EINVAL;
+    c->round_blocks = blocks;
     return KHCORE_OK;
 }
 

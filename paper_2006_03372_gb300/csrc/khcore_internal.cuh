@@ -355,7 +355,8 @@ int block_decompose_threads();
 
 // Cooperative launch of the whole decomposition; grid must not exceed
 // max_blocks_per_sm_persist(W) * SMs.
-cudaError_t launch_decompose_persist(int W, const PersistLaunch &L, int grid, cudaStream_t s);
-int max_blocks_per_sm_persist(int W);
+// minb: 2 selects the two-blocks-per-SM variant (W = 4 only), else one.
+cudaError_t launch_decompose_persist(int W, const PersistLaunch &L, int grid, cudaStream_t s, int minb);
+int max_blocks_per_sm_persist(int W, int minb);
 
 }  // namespace khc

@@ -126,7 +126,19 @@ struct BatchOpt {
     bool weights = false;       // lazy mode, seeded at the deleted set: ball bounds into wsum
     bool lazy_end = false;      // lazy mode, seeded at the deleted set: slack update of T at the end
     bool min_fold = false;      // fold the sources' h-degrees into their graph's exact minimum
+    bool pre_reset = false;     // the caller's last barrier already reset the ring for the first batch
 };
+
+// The level ring's reset for a batch of ns sources, in a barrier's serial step.
+__device__ __forceinline__ void reset_ring(LevelCtl *ctl, int32_t ns)
+{
+    for (int k = 0; k < 3; k++) {
+        ctl->q[k] = 0;
+        ctl->qi[k] = 0;
+        ctl->fe[k] = 0;
+    }
+    ctl->t = ns;
+}
 
 // One batch of the multi-source BFS (sources src[0..ns), h levels), every
 // block taking part, with fused levels (dev_level<W, LAST, true>): a barrier
@@ -144,16 +156,9 @@ __device__ bool bfs_batch(const PersistArgs &a, const int32_t *src, int32_t ns, 
     b.wdeg = a.deg;
     b.newcnt = o.lazy_end ? reinterpret_cast<unsigned long long *>(&a.ps->affected_total) : nullptr;
     LevelCtl *ctl = b.ctl;
-    // reset the level ring and place the sources (level 0)
-    if (!grid_sync(a.gs, a.timeout_ns, [&] {
-            for (int k = 0; k < 3; k++) {
-                ctl->q[k] = 0;
-                ctl->qi[k] = 0;
-                ctl->fe[k] = 0;
-            }
-            ctl->t = ns;
-        }))
-        return false;
+    // reset the level ring (unless the caller's barrier did) and place the
+    // sources (level 0)
+    if (!o.pre_reset && !grid_sync(a.gs, a.timeout_ns, [&] { reset_ring(ctl, ns); })) return false;
     {
         const int lane = threadIdx.x & 31;
         for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < ns; i0 += (int64_t)gridDim.x * blockDim.x) {
@@ -225,6 +230,7 @@ __device__ bool bfs_sources(const PersistArgs &a, const int32_t *src, int32_t ns
     for (int32_t off = 0; off < ns; off += S) {
         const int32_t cur = ns - off < S ? ns - off : S;
         o.row_first = row_first > off ? row_first - off : 0;
+        if (off > 0) o.pre_reset = false;  // only the first batch can be pre-reset
         // a batch of at most 64 sources runs on one-word rows: a quarter of
         // the row traffic of W = 4 for the same result (the row arrays are
         // all zero between batches in either layout)
@@ -240,16 +246,13 @@ __device__ bool bfs_sources(const PersistArgs &a, const int32_t *src, int32_t ns
 // inside a barrier (one barrier less per round).
 constexpr int32_t kSerialLevelMaxGraphs = 64;
 
-// Resident blocks of 512 threads per SM for the narrow rows (W <= 4). One
-// (up to 128 registers per thread, no spills, half the blocks at every grid
-// barrier) measured 4 % faster on the 1e6-vertex Chung-Lu graph at h = 2
-// than two blocks of 64 registers.
-#ifndef KHCORE_PERSIST_MIN_BLOCKS
-#define KHCORE_PERSIST_MIN_BLOCKS 1
-#endif
-
-template <int W>
-__global__ void __launch_bounds__(kBlock, (W <= 4 ? KHCORE_PERSIST_MIN_BLOCKS : 1)) k_decompose(PersistArgs a)
+// MINB: resident blocks of 512 threads per SM. One (up to 128 registers per
+// thread, no spills, half the blocks at every grid barrier) measured 4 %
+// faster than two (64 registers) on the 1e6-vertex Chung-Lu graph at h = 2,
+// where the rounds are latency-bound; two measured 14 % faster at h = 3 and 7 %
+// on the R-MAT graph at h = 4, where the rounds' BFS levels are larger.
+template <int W, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_decompose(PersistArgs a)
 {
     // phase clock of block 0: called right after a barrier, so the phase
     // before it is complete on every block
@@ -282,12 +285,16 @@ __global__ void __launch_bounds__(kBlock, (W <= 4 ? KHCORE_PERSIST_MIN_BLOCKS : 
             // selection
             if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
             dev_refine_select(a.g.n, a.alive, a.deg, a.p, a.cand);
+            // one class: the same serial step resets the BFS ring for the first
+            // batch of candidates (one barrier less)
             if (!grid_sync(a.gs, a.timeout_ns, [&] {
                     int32_t tot = 0;
                     for (int32_t c = 0; c < a.ncls; c++) tot += a.p.ncand[c];
                     if (tot == 0 && serial_level) {
                         dev_set_level_serial(a.p, a.st);
                         a.st->lvl_set = 1;
+                    } else if (a.ncls == 1) {
+                        reset_ring(a.b.ctl, tot < 64 * W ? tot : 64 * W);
                     }
                 }))
                 return;
@@ -298,6 +305,7 @@ __global__ void __launch_bounds__(kBlock, (W <= 4 ? KHCORE_PERSIST_MIN_BLOCKS : 
                     if (nc <= 0) continue;
                     BatchOpt o;
                     o.min_fold = true;
+                    o.pre_reset = a.ncls == 1;
                     if (!bfs_sources<W>(a, a.cand + a.cls_off[c], nc, a.cls_h[c], o)) return;
                     if (blockIdx.x == 0 && threadIdx.x == 0) a.ps->recomputed_total += nc;
                 }
@@ -330,9 +338,12 @@ __global__ void __launch_bounds__(kBlock, (W <= 4 ? KHCORE_PERSIST_MIN_BLOCKS : 
             // also widen their slack at the end of the batch (reading of
             // Observation 2: what they lose besides lies within h-1 of the
             // deleted set).
+            // one class: the statistics barrier also resets the BFS ring for
+            // the first batch seeded at the deleted set
             if (!grid_sync(a.gs, a.timeout_ns, [&] {
                     a.ps->rounds++;
                     a.ps->deleted_total += a.st->nD;
+                    if (a.ncls == 1) reset_ring(a.b.ctl, a.st->nD < 64 * W ? a.st->nD : 64 * W);
                 }))
                 return;
             mark(2);
@@ -341,6 +352,7 @@ __global__ void __launch_bounds__(kBlock, (W <= 4 ? KHCORE_PERSIST_MIN_BLOCKS : 
                 const int32_t nd = *((volatile int32_t *)&a.p.nDc[c]);
                 if (nd <= 0) continue;
                 BatchOpt o;
+                o.pre_reset = a.ncls == 1;
                 o.rowcnt = a.deg;
                 o.row_sign = -1;
                 o.weights = true;
@@ -406,7 +418,7 @@ __global__ void __launch_bounds__(kBlock, (W <= 4 ? KHCORE_PERSIST_MIN_BLOCKS : 
 }  // namespace
 
 // Per-W entry points, one translation unit each (khcore_persist_w*.cu).
-template <int W>
+template <int W, int MINB>
 cudaError_t persist_launch_w(const PersistLaunch &L, int grid, cudaStream_t s)
 {
     PersistArgs a;
@@ -438,14 +450,14 @@ cudaError_t persist_launch_w(const PersistLaunch &L, int grid, cudaStream_t s)
     a.ps = L.ps;
     a.timeout_ns = L.timeout_ns;
     void *args[] = {&a};
-    return cudaLaunchCooperativeKernel((const void *)k_decompose<W>, grid, kBlock, args, 0, s);
+    return cudaLaunchCooperativeKernel((const void *)k_decompose<W, MINB>, grid, kBlock, args, 0, s);
 }
 
-template <int W>
+template <int W, int MINB>
 int persist_occupancy_w()
 {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_decompose<W>, kBlock, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_decompose<W, MINB>, kBlock, 0) != cudaSuccess) {
         (void)cudaGetLastError();
         return 0;
     }
@@ -457,10 +469,12 @@ cudaError_t persist_launch_2(const PersistLaunch &L, int grid, cudaStream_t s);
 cudaError_t persist_launch_4(const PersistLaunch &L, int grid, cudaStream_t s);
 cudaError_t persist_launch_8(const PersistLaunch &L, int grid, cudaStream_t s);
 cudaError_t persist_launch_16(const PersistLaunch &L, int grid, cudaStream_t s);
+cudaError_t persist_launch_4x2(const PersistLaunch &L, int grid, cudaStream_t s);
 int persist_occupancy_1();
 int persist_occupancy_2();
 int persist_occupancy_4();
 int persist_occupancy_8();
 int persist_occupancy_16();
+int persist_occupancy_4x2();
 
 }  // namespace khc

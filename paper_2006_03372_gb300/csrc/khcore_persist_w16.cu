@@ -4,6 +4,6 @@
 #include "khcore_persist.cuh"
 
 namespace khc {
-cudaError_t persist_launch_16(const PersistLaunch &L, int grid, cudaStream_t s) { return persist_launch_w<16>(L, grid, s); }
-int persist_occupancy_16() { return persist_occupancy_w<16>(); }
+cudaError_t persist_launch_16(const PersistLaunch &L, int grid, cudaStream_t s) { return persist_launch_w<16, 1>(L, grid, s); }
+int persist_occupancy_16() { return persist_occupancy_w<16, 1>(); }
 }  // namespace khc

@@ -4,6 +4,6 @@
 #include "khcore_persist.cuh"
 
 namespace khc {
-cudaError_t persist_launch_2(const PersistLaunch &L, int grid, cudaStream_t s) { return persist_launch_w<2>(L, grid, s); }
-int persist_occupancy_2() { return persist_occupancy_w<2>(); }
+cudaError_t persist_launch_2(const PersistLaunch &L, int grid, cudaStream_t s) { return persist_launch_w<2, 1>(L, grid, s); }
+int persist_occupancy_2() { return persist_occupancy_w<2, 1>(); }
 }  // namespace khc

@@ -4,6 +4,6 @@
 #include "khcore_persist.cuh"
 
 namespace khc {
-cudaError_t persist_launch_4(const PersistLaunch &L, int grid, cudaStream_t s) { return persist_launch_w<4>(L, grid, s); }
-int persist_occupancy_4() { return persist_occupancy_w<4>(); }
+cudaError_t persist_launch_4(const PersistLaunch &L, int grid, cudaStream_t s) { return persist_launch_w<4, 1>(L, grid, s); }
+int persist_occupancy_4() { return persist_occupancy_w<4, 1>(); }
 }  // namespace khc

@@ -4,6 +4,6 @@
 #include "khcore_persist.cuh"
 
 namespace khc {
-cudaError_t persist_launch_8(const PersistLaunch &L, int grid, cudaStream_t s) { return persist_launch_w<8>(L, grid, s); }
-int persist_occupancy_8() { return persist_occupancy_w<8>(); }
+cudaError_t persist_launch_8(const PersistLaunch &L, int grid, cudaStream_t s) { return persist_launch_w<8, 1>(L, grid, s); }
+int persist_occupancy_8() { return persist_occupancy_w<8, 1>(); }
 }  // namespace khc

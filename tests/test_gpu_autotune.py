@@ -37,13 +37,29 @@ def test_knobs_do_not_change_results(kh):
                     assert np.array_equal(ctx.decompose(h), want_c), (g.name, h, light, medium, block)
 
 
+def test_round_kernel_residency_does_not_change_results(kh):
+    g = gg.chung_lu(6000, 8.0, 2.4, 300.0, 94)
+    for h in (2, 3):
+        want = oracle.peel(g, h)
+        rounds = None
+        for blocks in (1, 2):
+            with kh.KHCore.from_graph(g) as ctx:
+                kh.khcore_set_round_blocks(ctx.ctx, blocks)
+                c, r, _ = ctx.decompose_ex(h)
+            assert np.array_equal(c, want), (h, blocks)
+            if rounds is None:
+                rounds = r
+            assert np.array_equal(r, rounds), (h, blocks)
+
+
 def test_knob_arguments_are_checked(kh):
     g = gg.cycle(20)
     with kh.KHCore.from_graph(g) as ctx:
         for bad in [lambda: kh.khcore_set_degree_classes(ctx.ctx, 10, 5),
                     lambda: kh.khcore_set_degree_classes(ctx.ctx, -1, 5),
                     lambda: kh.khcore_set_block_size(ctx.ctx, 300),
-                    lambda: kh.khcore_set_block_graph_max(ctx.ctx, -2)]:
+                    lambda: kh.khcore_set_block_graph_max(ctx.ctx, -2),
+                    lambda: kh.khcore_set_round_blocks(ctx.ctx, 3)]:
             with pytest.raises(kh.KHCoreError):
                 bad()
 
