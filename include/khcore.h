@@ -305,9 +305,12 @@ khcore_status khcore_set_round_words(khcore_ctx *ctx, int32_t words);
  * khcore_set_push_alpha — direction choice of the multi-source BFS: a level
  * expands in the push direction (frontier vertices scatter to neighbours)
  * when (sum of frontier degrees) * alpha < CSR entries of the alive graph,
- * and in the pull direction (every alive vertex gathers) otherwise. Default
- * 16; 0 forces pull everywhere. alpha < 0 is EINVAL. Results do not depend
- * on alpha.
+ * and in the pull direction (every alive vertex gathers) otherwise. Sets it
+ * for every BFS of the context. Defaults: 16 for the all-vertex pass (its
+ * 16-word rows make push atomics dear) and 4 in the peel rounds (1- to 4-word
+ * rows; measured against 16: 20 % faster rounds on the 1e6-vertex Chung-Lu
+ * graph at h = 3, 7 % on a 97k-vertex batch graph at h = 4); 0 forces pull
+ * everywhere. alpha < 0 is EINVAL. Results do not depend on alpha.
  */
 khcore_status khcore_set_push_alpha(khcore_ctx *ctx, int32_t alpha);
 
@@ -348,6 +351,15 @@ khcore_status khcore_set_block_size(khcore_ctx *ctx, int32_t threads);
  * h <= 2, where the rounds are latency-bound, and 2 for h >= 3. EINVAL
  * otherwise. */
 khcore_status khcore_set_round_blocks(khcore_ctx *ctx, int32_t blocks);
+
+/* khcore_set_concurrent_graphs — batch contexts: the graphs above the
+ * per-block cut (khcore_set_block_graph_max) are decomposed k at a time
+ * (1..64, default 1), each in a context of its own on its own CUDA stream and
+ * host thread, its persistent round kernel on sm_count / k SMs. (On the
+ * 1,024-graph batch the default measured best: 250 s for k = 1, 266 s for
+ * k = 8, 410 s for k = 16 — its time sits in the largest graphs at h = 4,
+ * whose rounds keep the whole GPU busy.) EINVAL otherwise. */
+khcore_status khcore_set_concurrent_graphs(khcore_ctx *ctx, int32_t k);
 
 /* khcore_set_block_graph_max — batch contexts: graphs of at most nmax
  * vertices are decomposed by one thread block each (default 4096; see
@@ -457,7 +469,8 @@ khcore_status khcore_set_round_loop(khcore_ctx *ctx, int32_t mode);
  * (one launch over the union). Contexts of one graph use the grid-wide path
  * unless mode is 1. Results are identical in every mode; the per-block path
  * recomputes the inner affected vertices eagerly (khcore_set_lazy and
- * khcore_set_round_loop do not apply to it). EINVAL for other modes.
+ * khcore_set_round_loop do not apply to it). The larger graphs run several at
+ * a time (khcore_set_concurrent_graphs). EINVAL for other modes.
  */
 khcore_status khcore_set_graph_blocks(khcore_ctx *ctx, int32_t mode);
 

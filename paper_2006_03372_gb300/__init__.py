@@ -34,6 +34,7 @@ __all__ = [
     "khcore_hdegrees_of", "khcore_hdegrees_ex", "khcore_hdegrees_static", "Server", "request_bytes",
     "khcore_set_update", "khcore_bitmap_update", "khcore_decompose_sampled", "khcore_set_degree_classes",
     "khcore_set_block_size", "khcore_set_block_graph_max", "khcore_autotune", "Tuning", "khcore_set_round_blocks",
+    "khcore_set_concurrent_graphs",
 ]
 
 STATUS = {0: "KHCORE_OK", 1: "KHCORE_EINVAL", 2: "KHCORE_ENOMEM", 3: "KHCORE_ECUDA",
@@ -126,6 +127,8 @@ def load_library(build_if_missing: bool = False):
         lib.khcore_set_degree_classes.restype = ctypes.c_int
         lib.khcore_set_block_size.argtypes = [P, i32]
         lib.khcore_set_block_size.restype = ctypes.c_int
+        lib.khcore_set_concurrent_graphs.argtypes = [P, i32]
+        lib.khcore_set_concurrent_graphs.restype = ctypes.c_int
         lib.khcore_set_round_blocks.argtypes = [P, i32]
         lib.khcore_set_round_blocks.restype = ctypes.c_int
         lib.khcore_set_block_graph_max.argtypes = [P, i32]
@@ -293,6 +296,12 @@ def khcore_set_degree_classes(ctx, light_max: int, medium_max: int) -> None:
 def khcore_set_block_size(ctx, threads: int) -> None:
     lib = load_library()
     _check(lib, ctx, lib.khcore_set_block_size(ctx, int(threads)))
+
+
+def khcore_set_concurrent_graphs(ctx, k: int) -> None:
+    """Batch contexts: larger graphs decomposed k at a time (own stream each)."""
+    lib = load_library()
+    _check(lib, ctx, lib.khcore_set_concurrent_graphs(ctx, int(k)))
 
 
 def khcore_set_round_blocks(ctx, blocks: int) -> None:

@@ -7,9 +7,12 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/khcore.h"
@@ -72,7 +75,7 @@ struct khcore_ctx {
     int32_t *cnt = nullptr;
     unsigned long long *edges = nullptr;  // device counter of plain-BFS-equivalent edges
     unsigned long long *alg = nullptr;    // device counter of algorithmic bytes of the BFS levels
-    int32_t push_alpha = 16;              // push when frontier degree sum * alpha < alive CSR entries
+    int32_t push_alpha = 4;               // push when frontier degree sum * alpha < alive CSR entries
     int32_t round_loop = 0;               // 0: one persistent launch per decomposition, 1: host-driven rounds
     int32_t graph_blocks = 0;             // 0: auto, 1: one thread block per graph, -1: never
     int32_t *voff_d = nullptr;            // [G+1] vertex offsets (int32) for the per-block path
@@ -90,8 +93,10 @@ struct khcore_ctx {
     int32_t medium_max = kMediumMax;
     int32_t block = kBlock;               // threads per block of the per-phase BFS kernels
     int32_t block_graph_max = kBlockGraphsMaxN;  // batches: graphs decomposed by one thread block
-    int32_t init_alpha = 0;               // push alpha of the all-vertex pass (0: push_alpha)
+    int32_t init_alpha = 16;              // push alpha of the all-vertex pass (0: push_alpha)
     int32_t round_blocks = 0;             // round kernel blocks per SM (0: by h)
+    int32_t persist_sms = 0;              // SMs the round kernel's grid covers (0: all)
+    int32_t concurrent = 1;               // batches: larger graphs decomposed at once
     int32_t *class_counts = nullptr;      // [6] scratch of the class builder
     // the sampling variant (Algorithms 5 and 6): sample bytes, select at the
     // start and now, exact h-degrees at the start, the per-batch mask of the
@@ -683,29 +688,35 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
 // Graph gi of a batch context decomposed alone on the grid-wide path: a
 // context of its own over a copy of its CSR (local ids), the same stream and
 // settings; core indices and rounds go straight into c->core / c->rnd.
-// A context of its own over a copy of graph gi's CSR (local ids), on the same
-// stream and with c's settings.
-khcore_status make_sub(khcore_ctx *c, int32_t gi, khcore_ctx **out)
+// A context of its own over a copy of graph gi's CSR (local ids), on `stream`
+// (NULL: c's stream) and with c's settings. Only reads c's graph, so several
+// threads may make sub-contexts of one context at once (each on its own
+// stream); failures are reported through the return value only.
+khcore_status make_sub(khcore_ctx *c, int32_t gi, khcore_ctx **out, cudaStream_t stream = nullptr)
 {
     *out = nullptr;
+    cudaStream_t st = stream ? stream : c->stream;
     const int64_t v0 = c->v_off[gi];
     const int32_t ng = (int32_t)(c->v_off[gi + 1] - v0);
     std::vector<int32_t> rp((size_t)ng + 1);
-    CU(cudaMemcpyAsync(rp.data(), c->row_ptr + v0, sizeof(int32_t) * rp.size(), cudaMemcpyDeviceToHost, c->stream));
-    CU(cudaStreamSynchronize(c->stream));
+    if (cudaMemcpyAsync(rp.data(), c->row_ptr + v0, sizeof(int32_t) * rp.size(), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return KHCORE_ECUDA;
     const int32_t e0 = rp[0];
     for (auto &x : rp) x -= e0;
     std::vector<int32_t> col((size_t)rp[ng]);
     if (!col.empty()) {
-        CU(cudaMemcpyAsync(col.data(), c->col + e0, sizeof(int32_t) * col.size(), cudaMemcpyDeviceToHost,
-                           c->stream));
-        CU(cudaStreamSynchronize(c->stream));
+        if (cudaMemcpyAsync(col.data(), c->col + e0, sizeof(int32_t) * col.size(), cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return KHCORE_ECUDA;
     }
     for (auto &x : col) x -= (int32_t)v0;
     khcore_ctx *sub = nullptr;
     khcore_status s = khcore_create(ng, rp.data(), col.empty() ? nullptr : col.data(), KHCORE_FLAG_TRUST_INPUT,
-                                    c->stream, &sub);
-    if (s != KHCORE_OK) return fail(c, s, "graph %d alone: %s", gi, khcore_last_error(nullptr));
+                                    st, &sub);
+    if (s != KHCORE_OK) return s;
     sub->W_req = c->W_req;
     sub->Wr_req = c->Wr_req;
     sub->push_alpha = c->push_alpha;
@@ -726,7 +737,7 @@ khcore_status decompose_alone(khcore_ctx *c, int32_t gi, int32_t h, khcore_stats
 {
     khcore_ctx *sub = nullptr;
     khcore_status s = make_sub(c, gi, &sub);
-    if (s != KHCORE_OK) return s;
+    if (s != KHCORE_OK) return fail(c, s, "graph %d alone: %s", gi, khcore_last_error(nullptr));
     const int64_t v0 = c->v_off[gi];
     s = decompose(sub, std::vector<int32_t>{h}, c->core + v0, c->rnd + v0, sst);
     if (s != KHCORE_OK) {
@@ -907,11 +918,8 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         stt.deleted_total += c->n;
         khcore_stats sub_sum;
         std::memset(&sub_sum, 0, sizeof sub_sum);
-        std::vector<int32_t> kg_large;
-        for (int32_t gi : large) {
-            khcore_stats sst;
-            if ((s = decompose_alone(c, gi, h_in[gi], &sst)) != KHCORE_OK) return s;
-            kg_large.push_back(sst.k_max);
+        std::vector<int32_t> kg_large(large.size(), 0);
+        auto add_stats = [&](const khcore_stats &sst) {
             stt.rounds = std::max(stt.rounds, sst.rounds);
             stt.source_batches += sst.source_batches;
             stt.kernel_launches += sst.kernel_launches;
@@ -920,6 +928,78 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
             sub_sum.edges_traversed += sst.edges_traversed;
             sub_sum.level_bytes += sst.level_bytes;
             sub_sum.round_bytes += sst.round_bytes;
+        };
+        const int K = (int)std::min<size_t>(std::max(c->concurrent, 1), large.size());
+        if (K <= 1) {
+            for (size_t i = 0; i < large.size(); i++) {
+                khcore_stats sst;
+                if ((s = decompose_alone(c, large[i], h_in[large[i]], &sst)) != KHCORE_OK) return s;
+                kg_large[i] = sst.k_max;
+                add_stats(sst);
+            }
+        } else {
+            // K larger graphs at a time, each in a context of its own on its
+            // own stream, its round kernel on sm_count / K SMs: one graph's
+            // rounds are latency-bound and leave most of the GPU idle
+            std::atomic<size_t> next{0};
+            std::mutex mu;
+            khcore_status first = KHCORE_OK;
+            std::string first_msg;
+            auto worker = [&]() {
+                cudaSetDevice(c->device);
+                cudaStream_t st = nullptr;
+                if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+                    std::lock_guard<std::mutex> lk(mu);
+                    if (first == KHCORE_OK) {
+                        first = KHCORE_ECUDA;
+                        first_msg = "cudaStreamCreate failed";
+                    }
+                    return;
+                }
+                for (;;) {
+                    {
+                        std::lock_guard<std::mutex> lk(mu);
+                        if (first != KHCORE_OK) break;
+                    }
+                    const size_t i = next++;
+                    if (i >= large.size()) break;
+                    const int32_t gi = large[i];
+                    khcore_ctx *sub = nullptr;
+                    khcore_status ws = make_sub(c, gi, &sub, st);
+                    khcore_stats sst;
+                    std::memset(&sst, 0, sizeof sst);
+                    std::string msg;
+                    if (ws == KHCORE_OK) {
+                        sub->persist_sms = std::max(1, c->sm_count / K);
+                        const int64_t v0 = c->v_off[gi];
+                        ws = decompose(sub, std::vector<int32_t>{h_in[gi]}, c->core + v0, c->rnd + v0, &sst);
+                        if (ws != KHCORE_OK) msg = sub->err;
+                    } else {
+                        msg = khcore_last_error(nullptr);
+                    }
+                    khcore_destroy(sub);
+                    std::lock_guard<std::mutex> lk(mu);
+                    if (ws != KHCORE_OK) {
+                        if (first == KHCORE_OK) {
+                            first = ws;
+                            char buf[64];
+                            snprintf(buf, sizeof buf, "graph %d: ", gi);
+                            first_msg = buf + msg;
+                        }
+                        break;
+                    }
+                    kg_large[i] = sst.k_max;
+                    add_stats(sst);
+                }
+                cudaStreamDestroy(st);
+            };
+            std::vector<std::thread> pool;
+            for (int t = 0; t < K; t++) pool.emplace_back(worker);
+            for (auto &t : pool) t.join();
+            if (first != KHCORE_OK) {
+                if (first == KHCORE_ETIMEOUT) c->dirty = true;
+                return fail(c, first, "%s", first_msg.c_str());
+            }
         }
         for (size_t i = 0; i < large.size(); i++)
             CU(cudaMemcpyAsync(c->kg + large[i], &kg_large[i], sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
@@ -966,7 +1046,8 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
     // rounds are latency-bound (h <= 2), two for the larger BFS levels of h >= 3
     const int minb = c->round_blocks ? c->round_blocks : (hmax >= 3 ? 2 : 1);
     const int pgrid = (c->round_loop == 0 && !paper_update && !sampled)
-                          ? c->sm_count * max_blocks_per_sm_persist(Wr, minb)
+                          ? (c->persist_sms ? std::min(c->persist_sms, c->sm_count) : c->sm_count) *
+                                max_blocks_per_sm_persist(Wr, minb)
                           : 0;
     if (pgrid > 0) {
         // the whole decomposition in one cooperative launch
@@ -1380,6 +1461,7 @@ khcore_status khcore_set_push_alpha(khcore_ctx *c, int32_t alpha)
     if (!c) return KHCORE_EINVAL;
     if (alpha < 0) return fail(c, KHCORE_EINVAL, "alpha must be >= 0 (got %d)", alpha);
     c->push_alpha = alpha;
+    c->init_alpha = 0;  // the all-vertex pass follows
     return KHCORE_OK;
 }
 
@@ -1421,6 +1503,13 @@ khcore_status khcore_set_round_blocks(khcore_ctx *c, int32_t blocks)
 {
     if (!c || blocks < 0 || blocks > 2) return KHCORE_EINVAL;
     c->round_blocks = blocks;
+    return KHCORE_OK;
+}
+
+khcore_status khcore_set_concurrent_graphs(khcore_ctx *c, int32_t k)
+{
+    if (!c || k < 1 || k > 64) return KHCORE_EINVAL;
+    c->concurrent = k;
     return KHCORE_OK;
 }
 
@@ -1607,7 +1696,8 @@ khcore_status khcore_autotune(khcore_ctx *c, int32_t h, const char *cache_path, 
             double ms[2] = {0, 0};
             for (int mode = 0; mode < 2; mode++) {
                 khcore_ctx *sub = nullptr;
-                if ((s = make_sub(c, gi, &sub)) != KHCORE_OK) return s;
+                if ((s = make_sub(c, gi, &sub)) != KHCORE_OK)
+                    return fail(c, s, "autotune, graph %d: %s", gi, khcore_last_error(nullptr));
                 sub->graph_blocks = mode == 0 ? 1 : 0;  // 1: one thread block; 0: the grid-wide path
                 khcore_stats st;
                 for (int rep = 0; rep < 2 && s == KHCORE_OK; rep++)

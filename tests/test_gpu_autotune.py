@@ -23,8 +23,8 @@ def kh():
 
 
 def test_knobs_do_not_change_results(kh):
-    graphs = small_graphs(950, 5, (40, 400)) + [gg.disjoint_union(gg.star(1500), gg.chung_lu(3000, 7.0, 2.2,
-                                                                                              900.0, 95))]
+    graphs = small_graphs(950, 5, (40, 400)) + [gg.disjoint_union(gg.star(1100), gg.chung_lu(900, 6.0, 2.2,
+                                                                                              300.0, 95))]
     for g in graphs:
         for h in (2, 3):
             want_d, want_c = oracle.hdegrees(g, h), oracle.peel(g, h)
@@ -38,7 +38,7 @@ def test_knobs_do_not_change_results(kh):
 
 
 def test_round_kernel_residency_does_not_change_results(kh):
-    g = gg.chung_lu(6000, 8.0, 2.4, 300.0, 94)
+    g = gg.chung_lu(1500, 7.0, 2.4, 150.0, 94)
     for h in (2, 3):
         want = oracle.peel(g, h)
         rounds = None
