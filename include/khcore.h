@@ -104,6 +104,9 @@ typedef struct {
      * [2] peel-set compaction, [3] affected-set BFS, [4] h-degree update. */
     double phase_ms[5];
     int64_t grid_barriers;     /* grid-wide barriers the persistent kernel passed */
+    int32_t round_words;       /* W of the peel rounds' BFS batches */
+    int32_t round_blocks;      /* resident blocks per SM of the persistent round kernel
+                                  (0: the rounds were not run by it) */
 } khcore_stats;
 
 /*
@@ -366,7 +369,9 @@ khcore_status khcore_set_concurrent_graphs(khcore_ctx *ctx, int32_t k);
  * khcore_set_graph_blocks). EINVAL for nmax < 0. */
 khcore_status khcore_set_block_graph_max(khcore_ctx *ctx, int32_t nmax);
 
-/* The knobs khcore_autotune chose. */
+/* The knobs khcore_autotune chose (they apply to the all-vertex pass: its
+ * W, block size, degree classes and push alpha; the peel rounds keep theirs,
+ * and khcore_set_degree_classes / khcore_set_push_alpha set both). */
 typedef struct {
     int32_t words;            /* W of the all-vertex pass (khcore_set_words) */
     int32_t block;            /* khcore_set_block_size */

@@ -67,7 +67,8 @@ class Stats(ctypes.Structure):
                 ("level_ms", ctypes.c_double), ("level_bytes", ctypes.c_double),
                 ("recomputed_total", ctypes.c_int64), ("init_ms", ctypes.c_double),
                 ("round_ms", ctypes.c_double), ("round_bytes", ctypes.c_double),
-                ("phase_ms", ctypes.c_double * 5), ("grid_barriers", ctypes.c_int64)]
+                ("phase_ms", ctypes.c_double * 5), ("grid_barriers", ctypes.c_int64),
+                ("round_words", ctypes.c_int32), ("round_blocks", ctypes.c_int32)]
 
     def as_dict(self):
         out = {k: getattr(self, k) for k, _ in self._fields_}

@@ -62,6 +62,7 @@ struct khcore_ctx {
 
     // BFS buffers, sized for W_alloc words per vertex
     int W_req = 0;   // 0 = automatic
+    int W_av = 0;    // the all-vertex pass's W chosen by khcore_autotune (0 = none)
     int Wr_req = 0;  // W of the peel rounds, 0 = automatic
     int W_alloc = 0;
     uint64_t *V = nullptr, *F[2] = {nullptr, nullptr};
@@ -118,19 +119,27 @@ struct khcore_ctx {
     double level_ms = 0.0;
     int64_t level_launches = 0;
 
-    GraphView view() const
+    // degree classes of the all-vertex pass when tuned apart from the rounds'
+    // (khcore_autotune); nullptr: the same lists
+    int32_t *classes_av = nullptr;
+    int32_t n_light_av = 0, n_medium_av = 0, n_heavy_av = 0;
+
+    GraphView view(bool all_vertex = false) const
     {
+        const bool av = all_vertex && classes_av;
         GraphView g;
         g.n = n;
         g.m = m;
         g.row_ptr = row_ptr;
         g.col = col;
-        g.light = classes;
-        g.medium = classes + n_light;
-        g.heavy = classes + n_light + n_medium;
-        g.n_light = n_light;
-        g.n_medium = n_medium;
-        g.n_heavy = n_heavy;
+        const int32_t *cl = av ? classes_av : classes;
+        const int32_t nl = av ? n_light_av : n_light, nm = av ? n_medium_av : n_medium;
+        g.light = cl;
+        g.medium = cl + nl;
+        g.heavy = cl + nl + nm;
+        g.n_light = nl;
+        g.n_medium = nm;
+        g.n_heavy = av ? n_heavy_av : n_heavy;
         return g;
     }
 };
@@ -358,7 +367,7 @@ khcore_status hdeg_sources(khcore_ctx *c, int W, int32_t h, const int32_t *src, 
                            int64_t m_b, khcore_stats *stt, int32_t *rowcnt = nullptr, int32_t row_first = 0,
                            int32_t *wsum = nullptr, bool all_vertex = false)
 {
-    const GraphView g = c->view();
+    const GraphView g = c->view(all_vertex);
     BfsBufs b;
     b.V = c->V;
     b.F[0] = c->F[0];
@@ -718,6 +727,7 @@ khcore_status make_sub(khcore_ctx *c, int32_t gi, khcore_ctx **out, cudaStream_t
                                     st, &sub);
     if (s != KHCORE_OK) return s;
     sub->W_req = c->W_req;
+    sub->W_av = c->W_av;
     sub->Wr_req = c->Wr_req;
     sub->push_alpha = c->push_alpha;
     sub->lazy = c->lazy;
@@ -793,9 +803,10 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         if (stats) *stats = stt;
         return KHCORE_OK;
     }
-    const int W = c->W_req ? c->W_req : auto_words(c->n);
+    const int W = c->W_req ? c->W_req : (c->W_av ? c->W_av : auto_words(c->n));
     const int Wr = c->Wr_req ? c->Wr_req : (c->W_req ? c->W_req : auto_round_words(c->n));
     stt.words_per_vertex = W;
+    stt.round_words = Wr;
     khcore_status s;
     if ((s = ensure_bfs(c, std::max(W, Wr))) != KHCORE_OK) return s;
     if ((s = clear_if_dirty(c)) != KHCORE_OK) return s;
@@ -1131,6 +1142,7 @@ khcore_status decompose(khcore_ctx *c, const std::vector<int32_t> &h_in, int32_t
         stt.affected_total += psh.affected_total;
         for (int k = 0; k < 5; k++) stt.phase_ms[k] = (double)psh.phase_ns[k] * 1e-6;
         stt.grid_barriers = (int64_t)gsh.passed;
+        stt.round_blocks = minb;
         return finish_decompose(c, G, core_out, round_out, stats, stt, true);
     }
 
@@ -1347,7 +1359,7 @@ void khcore_destroy(khcore_ctx *c)
                     c->Fx, c->flagx, c->tflag, c->flag[0], c->flag[1], c->Q[0], c->Q[1], c->Q[2], c->I[0], c->I[1], c->I[2], c->T, c->ctl,
                     c->cnt, c->edges, c->alg};
     for (void *p : bufs) cudaFree(p);
-    void *sbufs[] = {c->s_in, c->s_sel0, c->s_sel, c->s_d0, c->s_full, c->class_counts};
+    void *sbufs[] = {c->s_in, c->s_sel0, c->s_sel, c->s_d0, c->s_full, c->class_counts, c->classes_av};
     for (void *p : sbufs) cudaFree(p);
     void *ubufs[] = {c->upd.vis, c->upd.list, c->upd.dist, c->upd.reach, c->upd.meta, c->upd.owner, c->upd.lab,
                      c->upd.done, c->upd.flag, c->upd.cand[0], c->upd.cand[1]};
@@ -1472,6 +1484,35 @@ khcore_status khcore_set_lazy(khcore_ctx *c, int32_t on)
     return KHCORE_OK;
 }
 
+namespace {
+
+// Rebuild a degree-class list (the rounds' when all_vertex is false, else the
+// all-vertex pass's own).
+khcore_status build_classes(khcore_ctx *c, int32_t light_max, int32_t medium_max, bool all_vertex)
+{
+    if (!c->class_counts) CU(dev_alloc(&c->class_counts, 6));
+    if (all_vertex && !c->classes_av) CU(dev_alloc(&c->classes_av, (size_t)std::max(c->n, 1)));
+    int32_t *dst = all_vertex ? c->classes_av : c->classes;
+    int32_t cnt[3] = {0, 0, 0};
+    CU(launch_degree_classes(c->row_ptr, c->n, light_max, medium_max, dst, c->class_counts, c->stream));
+    CU(cudaMemcpyAsync(cnt, c->class_counts, sizeof cnt, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (all_vertex) {
+        c->n_light_av = cnt[0];
+        c->n_medium_av = cnt[1];
+        c->n_heavy_av = cnt[2];
+    } else {
+        c->n_light = cnt[0];
+        c->n_medium = cnt[1];
+        c->n_heavy = cnt[2];
+        c->light_max = light_max;
+        c->medium_max = medium_max;
+    }
+    return KHCORE_OK;
+}
+
+}  // namespace
+
 khcore_status khcore_set_degree_classes(khcore_ctx *c, int32_t light_max, int32_t medium_max)
 {
     khcore_status s;
@@ -1479,16 +1520,9 @@ khcore_status khcore_set_degree_classes(khcore_ctx *c, int32_t light_max, int32_
     if (light_max < 0 || medium_max < light_max)
         return fail(c, KHCORE_EINVAL, "degree classes need 0 <= light_max <= medium_max (got %d, %d)", light_max,
                     medium_max);
-    if (!c->class_counts) CU(dev_alloc(&c->class_counts, 6));
-    int32_t cnt[3] = {0, 0, 0};
-    CU(launch_degree_classes(c->row_ptr, c->n, light_max, medium_max, c->classes, c->class_counts, c->stream));
-    CU(cudaMemcpyAsync(cnt, c->class_counts, sizeof cnt, cudaMemcpyDeviceToHost, c->stream));
-    CU(cudaStreamSynchronize(c->stream));
-    c->n_light = cnt[0];
-    c->n_medium = cnt[1];
-    c->n_heavy = cnt[2];
-    c->light_max = light_max;
-    c->medium_max = medium_max;
+    if ((s = build_classes(c, light_max, medium_max, false)) != KHCORE_OK) return s;
+    cudaFree(c->classes_av);  // every BFS of the context uses these lists now
+    c->classes_av = nullptr;
     return KHCORE_OK;
 }
 
@@ -1580,7 +1614,7 @@ khcore_status khcore_autotune(khcore_ctx *c, int32_t h, const char *cache_path, 
     if (h < 1) return fail(c, KHCORE_EINVAL, "h must be >= 1 (got %d)", h);
     khcore_tuning t;
     std::memset(&t, 0, sizeof t);
-    t.words = c->W_req ? c->W_req : auto_words(c->n);
+    t.words = c->W_req ? c->W_req : (c->W_av ? c->W_av : auto_words(c->n));
     t.block = c->block;
     t.light_max = c->light_max;
     t.medium_max = c->medium_max;
@@ -1623,7 +1657,7 @@ khcore_status khcore_autotune(khcore_ctx *c, int32_t h, const char *cache_path, 
         CU(cudaEventCreate(&e1));
         auto trial = [&](const khcore_tuning &k, float *ms) -> khcore_status {
             khcore_status st;
-            if ((st = khcore_set_degree_classes(c, k.light_max, k.medium_max)) != KHCORE_OK) return st;
+            if ((st = build_classes(c, k.light_max, k.medium_max, true)) != KHCORE_OK) return st;
             c->block = k.block;
             c->init_alpha = k.push_alpha;
             float best = 1e30f;
@@ -1718,9 +1752,9 @@ khcore_status khcore_autotune(khcore_ctx *c, int32_t h, const char *cache_path, 
         if (!pick.empty()) t.block_graph_max = cut;
         cache_store(cache_path, key, t);
     }
-    // apply
-    if ((s = khcore_set_degree_classes(c, t.light_max, t.medium_max)) != KHCORE_OK) return s;
-    c->W_req = t.words;
+    // apply: the all-vertex pass takes the tuned classes, the rounds keep theirs
+    if ((s = build_classes(c, t.light_max, t.medium_max, true)) != KHCORE_OK) return s;
+    c->W_av = t.words;  // the all-vertex pass only; the rounds keep their W
     c->block = t.block;
     c->init_alpha = t.push_alpha;
     c->block_graph_max = t.block_graph_max;
@@ -1829,7 +1863,7 @@ khcore_status khcore_hdegrees_ex(khcore_ctx *c, int32_t h, int32_t *deg_out, khc
         if (stats) *stats = stt;
         return KHCORE_OK;
     }
-    const int W = c->W_req ? c->W_req : auto_words(c->n);
+    const int W = c->W_req ? c->W_req : (c->W_av ? c->W_av : auto_words(c->n));
     if ((s = ensure_bfs(c, W)) != KHCORE_OK) return s;
     if ((s = clear_if_dirty(c)) != KHCORE_OK) return s;
     int32_t hmax = 1;
@@ -1893,7 +1927,7 @@ khcore_status khcore_hdegrees_of(khcore_ctx *c, int32_t h, int32_t count, const 
             if (seen[vs[i]]++) return fail(c, KHCORE_EINVAL, "vertex %d listed twice", vs[i]);
         }
     }
-    const int W = c->W_req ? c->W_req : auto_words(c->n);
+    const int W = c->W_req ? c->W_req : (c->W_av ? c->W_av : auto_words(c->n));
     if ((s = ensure_bfs(c, W)) != KHCORE_OK) return s;
     if ((s = clear_if_dirty(c)) != KHCORE_OK) return s;
     int32_t hmax = 1;
