@@ -592,28 +592,27 @@ def run_serve(args):
     graphs = [gg.request_graph(r) for r in reqs]  # generated off the clock
     gen_s = time.perf_counter() - t0
     srv = kh.Server(int(args.budget_gb * 2 ** 30), slots=args.slots)
-    tickets = []
+    pending = {}  # ticket -> (request, submit time relative to start)
     start = time.perf_counter()
     for r, g in zip(reqs, graphs):
         delay = start + r.arrival_s - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
-        tickets.append((srv.submit(g.n, g.row_ptr, g.col, r.h), r))
+        t = srv.submit(g.n, g.row_ptr, g.col, r.h)
+        pending[t] = (r, time.perf_counter() - start)
+    # collect every request as it finishes (the server's own finish - submit
+    # latency, plus the submit delay after the scheduled arrival)
     deadline = start + args.serve_seconds + args.serve_drain_s
     lat, done_at = [], []
-    unfinished = 0
-    for t, r in tickets:
-        left = deadline - time.perf_counter()
-        try:
-            if left <= 0:
-                raise TimeoutError
-            srv.wait(t, timeout_s=left)
-        except Exception:
-            unfinished += 1
-            continue
-        now = time.perf_counter() - start
-        lat.append((now - r.arrival_s) * 1e3)
-        done_at.append(now)
+    while pending and time.perf_counter() < deadline:
+        for t in [t for t in pending if srv.done(t)]:
+            r, sub = pending.pop(t)
+            _, server_ms = srv.wait(t, timeout_s=1.0)
+            fin = sub + server_ms / 1e3
+            lat.append((fin - r.arrival_s) * 1e3)
+            done_at.append(fin)
+        time.sleep(0.02)
+    unfinished = len(pending)
     wall = time.perf_counter() - start
     st = srv.stats()
     srv.close()

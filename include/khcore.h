@@ -498,13 +498,16 @@ khcore_status khcore_set_profiling(khcore_ctx *ctx, int32_t on);
  * Serving: a request server with continuous batching.
  *
  * Requests wait in arrival order. Each of `slots` worker threads owns a CUDA
- * stream on the device current at khcore_server_create; a free worker admits
- * every queued request that still fits the device-memory budget (at most
- * max_batch), decomposes them together as one batch context
- * (khcore_batch_create / khcore_batch_decompose) and publishes the results.
- * Workers run concurrently, so requests that arrive while others are on the
- * GPU are admitted as slots and budget free up, and their work overlaps on the
- * device. A request's core indices equal those of a solo khcore_decompose.
+ * stream on the device current at khcore_server_create. A free worker admits
+ * either every queued small request (at most 4,096 vertices) that still fits
+ * the device-memory budget, at most max_batch, and decomposes them together
+ * as one batch context (one thread block per graph, one launch), or, when no
+ * small request waits, the oldest large request that fits, decomposed alone
+ * on the grid-wide path; each finished unit is published at once. Workers run
+ * concurrently, so requests that arrive while others are on the GPU are
+ * admitted as slots and budget free up, a large request never holds small
+ * ones back, and their work overlaps on the device. A request's core indices
+ * equal those of a solo khcore_decompose.
  * ------------------------------------------------------------------------- */
 typedef struct khcore_server khcore_server;
 

@@ -120,16 +120,14 @@ void run_group(khcore_server *s, std::vector<Request *> &batch, cudaStream_t str
     s->cv_work.notify_all();  // budget freed
 }
 
-// An admitted group: the graphs small enough for one block each run as one
-// per-block batch, the rest as one grid-wide batch.
-void run_batch(khcore_server *s, std::vector<Request *> &batch, cudaStream_t stream)
-{
-    std::vector<Request *> small, large;
-    for (Request *r : batch) (r->n <= khc::kBlockGraphsMaxN ? small : large).push_back(r);
-    if (!small.empty()) run_group(s, small, stream, true);
-    if (!large.empty()) run_group(s, large, stream, false);
-}
+bool is_small(const Request *r) { return r->n <= khc::kBlockGraphsMaxN; }
 
+// A worker takes either every queued small request that fits the budget (up
+// to max_batch, in arrival order), decomposed together in one launch of one
+// thread block per graph, or, when no small request waits, the oldest large
+// request, decomposed alone on the grid-wide path. Each is published as soon
+// as its own work is done, so a large request never holds small ones back and
+// several large ones run at once on different slots.
 void worker_main(khcore_server *s)
 {
     cudaSetDevice(s->device);
@@ -137,23 +135,42 @@ void worker_main(khcore_server *s)
     if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) return;
     for (;;) {
         std::vector<Request *> batch;
+        bool small = false;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            s->cv_work.wait(lk, [&] {
-                return s->stop || (!s->queue.empty() && s->in_use + s->queue.front()->bytes <= s->budget);
-            });
+            auto admissible = [&](const Request *r) { return s->in_use + r->bytes <= s->budget; };
+            auto any_work = [&] {
+                for (const Request *r : s->queue)
+                    if (admissible(r)) return true;
+                return false;
+            };
+            s->cv_work.wait(lk, [&] { return s->stop || any_work(); });
             if (s->stop) break;  // queued requests are dropped by khcore_server_destroy
-            // admit in arrival order while the budget allows
-            while (!s->queue.empty() && (int32_t)batch.size() < s->max_batch &&
-                   s->in_use + s->queue.front()->bytes <= s->budget) {
-                Request *r = s->queue.front();
-                s->queue.pop_front();
-                s->in_use += r->bytes;
-                r->started = Clock::now();
-                batch.push_back(r);
+            for (auto it = s->queue.begin(); it != s->queue.end() && (int32_t)batch.size() < s->max_batch;) {
+                Request *r = *it;
+                if (is_small(r) && admissible(r)) {
+                    s->in_use += r->bytes;
+                    r->started = Clock::now();
+                    batch.push_back(r);
+                    it = s->queue.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+            small = !batch.empty();
+            if (!small) {
+                for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+                    Request *r = *it;
+                    if (!admissible(r)) continue;
+                    s->in_use += r->bytes;
+                    r->started = Clock::now();
+                    batch.push_back(r);
+                    s->queue.erase(it);
+                    break;
+                }
             }
         }
-        if (!batch.empty()) run_batch(s, batch, stream);
+        if (!batch.empty()) run_group(s, batch, stream, small);
     }
     cudaStreamDestroy(stream);
 }
