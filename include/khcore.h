@@ -355,6 +355,14 @@ khcore_status khcore_set_block_size(khcore_ctx *ctx, int32_t threads);
  * otherwise. */
 khcore_status khcore_set_round_blocks(khcore_ctx *ctx, int32_t blocks);
 
+/* khcore_set_round_sms — SMs the persistent round kernel's grid covers: 1 up
+ * to the device's SM count, or 0 (default) for all of them. Fewer blocks make
+ * each grid barrier cheaper (fewer arrivals on its counter) and each scan
+ * phase longer. Batch contexts that run graphs concurrently size their
+ * graphs' kernels themselves (khcore_set_concurrent_graphs). EINVAL
+ * otherwise. */
+khcore_status khcore_set_round_sms(khcore_ctx *ctx, int32_t sms);
+
 /* khcore_set_concurrent_graphs — batch contexts: the graphs above the
  * per-block cut (khcore_set_block_graph_max) are decomposed k at a time
  * (1..64, default 1), each in a context of its own on its own CUDA stream and

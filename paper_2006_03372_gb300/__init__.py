@@ -34,7 +34,7 @@ __all__ = [
     "khcore_hdegrees_of", "khcore_hdegrees_ex", "khcore_hdegrees_static", "Server", "request_bytes",
     "khcore_set_update", "khcore_bitmap_update", "khcore_decompose_sampled", "khcore_set_degree_classes",
     "khcore_set_block_size", "khcore_set_block_graph_max", "khcore_autotune", "Tuning", "khcore_set_round_blocks",
-    "khcore_set_concurrent_graphs",
+    "khcore_set_concurrent_graphs", "khcore_set_round_sms",
 ]
 
 STATUS = {0: "KHCORE_OK", 1: "KHCORE_EINVAL", 2: "KHCORE_ENOMEM", 3: "KHCORE_ECUDA",
@@ -132,6 +132,8 @@ def load_library(build_if_missing: bool = False):
         lib.khcore_set_concurrent_graphs.restype = ctypes.c_int
         lib.khcore_set_round_blocks.argtypes = [P, i32]
         lib.khcore_set_round_blocks.restype = ctypes.c_int
+        lib.khcore_set_round_sms.argtypes = [P, i32]
+        lib.khcore_set_round_sms.restype = ctypes.c_int
         lib.khcore_set_block_graph_max.argtypes = [P, i32]
         lib.khcore_set_block_graph_max.restype = ctypes.c_int
         lib.khcore_autotune.argtypes = [P, i32, ctypes.c_char_p, ctypes.POINTER(Tuning)]
@@ -309,6 +311,12 @@ def khcore_set_round_blocks(ctx, blocks: int) -> None:
     """Resident blocks per SM of the round kernel (0: by h, 1 or 2)."""
     lib = load_library()
     _check(lib, ctx, lib.khcore_set_round_blocks(ctx, int(blocks)))
+
+
+def khcore_set_round_sms(ctx, sms: int) -> None:
+    """SMs the round kernel's grid covers (0: all)."""
+    lib = load_library()
+    _check(lib, ctx, lib.khcore_set_round_sms(ctx, int(sms)))
 
 
 def khcore_set_block_graph_max(ctx, nmax: int) -> None:

@@ -1540,6 +1540,13 @@ khcore_status khcore_set_round_blocks(khcore_ctx *c, int32_t blocks)
     return KHCORE_OK;
 }
 
+khcore_status khcore_set_round_sms(khcore_ctx *c, int32_t sms)
+{
+    if (!c || sms < 0 || sms > c->sm_count) return KHCORE_EINVAL;
+    c->persist_sms = sms;
+    return KHCORE_OK;
+}
+
 khcore_status khcore_set_concurrent_graphs(khcore_ctx *c, int32_t k)
 {
     if (!c || k < 1 || k > 64) return KHCORE_EINVAL;

@@ -222,6 +222,46 @@ __device__ __forceinline__ void append_frontier(bool pred, int32_t y, int32_t de
     if (pred) acc.fe += (unsigned long long)deg;
 }
 
+// Fused push levels before the last: append y to the next frontier list Q
+// (claimed) with its CSR row as push work items (row [e0, e0 + dy)), and to
+// T (first), with the three list counters taken in one atomic round trip
+// per warp. Whole warp calls.
+template <int W>
+__device__ __forceinline__ void append_next_and_touched(bool claimed, bool first, int32_t y, int32_t e0, int32_t dy,
+                                                        const BfsBufs &b, int nslot, Acc &acc)
+{
+    constexpr int C = push_chunk(W);
+    const int lane = threadIdx.x & 31;
+    const unsigned mq = __ballot_sync(kFull, claimed), mt = __ballot_sync(kFull, first);
+    if (!(mq | mt)) return;  // warp-uniform
+    const int32_t nch = claimed ? (dy + C - 1) / C : 0;
+    int32_t incl = nch;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int32_t t = __shfl_up_sync(kFull, incl, off);
+        if (lane >= off) incl += t;
+    }
+    const int32_t total = __shfl_sync(kFull, incl, 31);
+    int32_t bq = 0, bi = 0, bt = 0;
+    if (lane == 0) {  // independent atomics: issued back to back
+        if (mq) bq = atomicAdd(&b.ctl->q[nslot], __popc(mq));
+        if (total) bi = atomicAdd(&b.ctl->qi[nslot], total);
+        if (mt) bt = atomicAdd(&b.ctl->t, __popc(mt));
+    }
+    bq = __shfl_sync(kFull, bq, 0);
+    bi = __shfl_sync(kFull, bi, 0);
+    bt = __shfl_sync(kFull, bt, 0);
+    const unsigned lt = lanemask_lt();
+    if (claimed) pick3(b.Q, nslot)[bq + __popc(mq & lt)] = y;
+    if (first) b.T[bt + __popc(mt & lt)] = y;
+    if (nch) {
+        int2 *items = pick3(b.I, nslot);
+        const int32_t base = bi + incl - nch;
+        for (int32_t k = 0; k < nch; k++) items[base + k] = make_int2(y, e0 + k * C);
+    }
+    if (claimed) acc.fe += (unsigned long long)dy;
+}
+
 // OR the W words of frontier row x into a.
 template <int W>
 __device__ __forceinline__ void or_row(uint64_t (&a)[W], const uint64_t *F, int32_t x)
@@ -449,15 +489,17 @@ __device__ __forceinline__ T *ring3(T *a0, T *a1, T *a2, int i)
 
 // Clear the frontier rows and flags of the vertices listed in ring slot
 // `slot` (fused levels). W lanes per vertex.
+// rot shifts the work to other warps than those starting at warp 0, so that
+// its chain of loads runs beside the phase's other work instead of after it.
 template <int W>
-__device__ __forceinline__ void clear_slot(const BfsBufs &b, int slot)
+__device__ __forceinline__ void clear_slot(const BfsBufs &b, int slot, int32_t nq, int64_t rot)
 {
     const int lane = threadIdx.x & 31;
     const int j = lane % W, grp = lane / W;
     constexpr int VPW = 32 / W;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int32_t nq = b.ctl->q[slot];
+    int64_t warp = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) + rot % nwarps;
+    if (warp >= nwarps) warp -= nwarps;
     const int32_t *Qs = pick3(b.Q, slot);
     uint64_t *Fs = ring3(b.F[0], b.F[1], b.Fx, slot);
     uint32_t *fls = ring3(b.flag[0], b.flag[1], b.flagx, slot);
@@ -470,6 +512,10 @@ __device__ __forceinline__ void clear_slot(const BfsBufs &b, int slot)
         }
     }
 }
+
+// Fused push levels: frontier degree sum up to which the atomic on V is not
+// preceded by a load of V.
+constexpr unsigned long long kProbeEdges = 1ull << 15;
 
 template <int W, bool LAST, bool FUSED = false>
 __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, BfsBufs b,
@@ -486,9 +532,16 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
     uint64_t *Fn = FUSED ? ring3(b.F[0], b.F[1], b.Fx, nslot) : pick2(b.F, nb_);
     uint32_t *fln = FUSED ? ring3(b.flag[0], b.flag[1], b.flagx, nslot) : pick2(b.flag, nb_);
     uint64_t *V = b.V;
-    const bool push = use_push(b.ctl, cslot, tune);
+    // the frontier's list lengths, loaded together (one round trip)
+    const unsigned long long fe_c = b.ctl->fe[cslot];
+    const int32_t nq_c = b.ctl->q[cslot];
+    const int32_t ni = b.ctl->qi[cslot];
+    const int32_t nq_old = (FUSED && lvl > 0) ? b.ctl->q[(lvl + 2) % 3] : 0;
+    const bool push = tune.alpha > 0 && fe_c * (unsigned long long)tune.alpha < tune.m_alive;
 
-    if (FUSED && lvl > 0) clear_slot<W>(b, (lvl + 2) % 3);
+    // on the upper half of the warps: the push work items start at warp 0
+    if (FUSED && lvl > 0)
+        clear_slot<W>(b, (lvl + 2) % 3, nq_old, ((int64_t)gridDim.x * blockDim.x >> 5) / 2);
     for (int i = threadIdx.x; i < 64 * W; i += blockDim.x) cnt_s[i] = 0;
     // Algorithmic bytes of this level. Pull: 4 n_b (row offsets) + 4 m_b
     // (column ids) over the n_b alive rows and their m_b entries, 8 W per
@@ -501,8 +554,7 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
     if (blockIdx.x == 0 && threadIdx.x == 0 && b.alg_bytes) {
         const unsigned long long nb = (unsigned long long)tune.n_alive;
         const unsigned long long bytes =
-            push ? (unsigned long long)b.ctl->fe[cslot] * (4ull + 16ull * W) +
-                       (unsigned long long)b.ctl->q[cslot] * 8ull * W
+            push ? fe_c * (4ull + 16ull * W) + (unsigned long long)nq_c * 8ull * W
                  : 4ull * nb + 4ull * tune.m_alive;
         atomicAdd(b.alg_bytes, bytes);
     }
@@ -525,9 +577,9 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
         const int grp = slot;
         const unsigned gmask = (1u << W) - 1u;
         constexpr int C = push_chunk(W);
-        const int32_t ni = b.ctl->qi[cslot];
         const int2 *Ic = pick3(b.I, cslot);
-        // one edge of the expansion: y = col[e] gets fx & ~V(y)
+        // one edge of the expansion: y = col[e] gets fx & ~V(y) (per-phase
+        // levels, and the last fused level, which writes neither V nor T)
         auto edge = [&](int32_t e, int32_t e1, uint64_t fx) {
             int32_t y = -1;
             uint64_t nbits = 0, fresh = 0, v = 0;
@@ -541,9 +593,6 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
                             atomicOr(reinterpret_cast<unsigned long long *>(&Fn[(size_t)y * W + j]),
                                      (unsigned long long)nbits);
                         fresh = nbits & ~(uint64_t)old;
-                        if (FUSED && !LAST && fresh)
-                            atomicOr(reinterpret_cast<unsigned long long *>(&V[(size_t)y * W + j]),
-                                     (unsigned long long)fresh);
                         if (b.rowcnt) {
                             const uint64_t rf = fresh & row_mask(j, b.row_first);
                             if (rf) atomicAdd(&b.rowcnt[y], b.row_sign * __popcll(rf));
@@ -561,22 +610,60 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
                 dy = rp[y + 1] - rp[y];
             }
             append_frontier<W>(claimed, y, (FUSED && LAST) ? 0 : dy, b, nslot, acc, rp);
-            if constexpr (FUSED) {
+            if constexpr (FUSED && LAST) {
                 const unsigned vany = __ballot_sync(kFull, v != 0);
                 const bool gv = ((vany >> (grp * W)) & gmask) != 0;
-                if (!LAST) {
-                    // first visit of y in this batch: the touched list; and
-                    // the plain-BFS edges of the sources that reach it now
-                    const unsigned fany = __ballot_sync(kFull, fresh != 0);
-                    const bool gfresh = ((fany >> (grp * W)) & gmask) != 0;
-                    const bool first = (j == 0) && gfresh && flag_claim(b.tflag, y);
-                    warp_append(first, y, b.T, &b.ctl->t);
-                    const int32_t dyg = __shfl_sync(kFull, dy, lane & ~(W - 1));
-                    if (fresh) acc.scanned += (unsigned long long)__popcll(fresh) * (unsigned long long)dyg;
-                } else if (b.newcnt && claimed && !gv) {
-                    acc.newv++;
+                if (b.newcnt && claimed && !gv) acc.newv++;
+            }
+        };
+        // Fused levels before the last: V itself takes the atomicOr (its old
+        // value says which bits are new), the new bits go on into the next
+        // frontier row without a return value, and the frontier and
+        // touched-list claims, and then the three list appends, each take one
+        // round trip. Same result as edge: every bit is new for exactly one
+        // writer. A small frontier skips the load of V before the atomic (one
+        // round trip less); a large one keeps it, so that the atomics on
+        // much-visited rows stay few.
+        const bool probe = fe_c > kProbeEdges;
+        auto edge_fused = [&](int32_t e, int32_t e1, uint64_t fx) {
+            int32_t y = -1;
+            uint64_t fresh = 0;
+            if (e < e1) {
+                y = __ldg(&col[e]);
+                uint64_t nb = is_alive(alive, y) ? fx : 0;
+                if (probe && nb) nb &= ~V[(size_t)y * W + j];
+                if (nb) {
+                    const unsigned long long old = atomicOr(
+                        reinterpret_cast<unsigned long long *>(&V[(size_t)y * W + j]), (unsigned long long)nb);
+                    fresh = nb & ~(uint64_t)old;
+                    if (fresh) {
+                        atomicOr(reinterpret_cast<unsigned long long *>(&Fn[(size_t)y * W + j]),
+                                 (unsigned long long)fresh);
+                        if (b.rowcnt) {
+                            const uint64_t rf = fresh & row_mask(j, b.row_first);
+                            if (rf) atomicAdd(&b.rowcnt[y], b.row_sign * __popcll(rf));
+                        }
+                    }
                 }
             }
+            swar_step<W>(sw, fresh & elig_mask(b, j, y), cnt_s);
+            const unsigned fany = __ballot_sync(kFull, fresh != 0);
+            const bool lead = (j == 0) && (((fany >> (grp * W)) & gmask) != 0);
+            bool claimed = false, first = false;
+            int32_t e0 = 0, dy = 0;
+            if (lead) {
+                const uint32_t bit = 1u << (y & 31);
+                const uint32_t of = atomicOr(&fln[y >> 5], bit);
+                const uint32_t ot = atomicOr(&b.tflag[y >> 5], bit);
+                e0 = rp[y];
+                dy = rp[y + 1] - e0;
+                claimed = (of & bit) == 0;
+                first = (ot & bit) == 0;
+            }
+            append_next_and_touched<W>(claimed, first, y, e0, dy, b, nslot, acc);
+            // the plain-BFS edges of the sources that reach y now
+            const int32_t dyg = __shfl_sync(kFull, dy, lane & ~(W - 1));
+            if (fresh) acc.scanned += (unsigned long long)__popcll(fresh) * (unsigned long long)dyg;
         };
         // work items: up to C entries of one frontier row each, one warp per item
         for (int64_t it = warp; it < ni; it += nwarps) {  // warp-uniform
@@ -585,7 +672,12 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
             const int32_t rend = rp[x + 1];
             const int32_t e1 = item.y + C < rend ? item.y + C : rend;
             const uint64_t fx = Fc[(size_t)x * W + j];
-            for (int32_t eb = item.y; eb < e1; eb += SLOTS) edge(eb + slot, e1, fx);
+            for (int32_t eb = item.y; eb < e1; eb += SLOTS) {
+                if constexpr (FUSED && !LAST)
+                    edge_fused(eb + slot, e1, fx);
+                else
+                    edge(eb + slot, e1, fx);
+            }
         }
     } else {
         // ---------------- pull: every alive vertex gathers its neighbours ----
@@ -744,13 +836,16 @@ __device__ __forceinline__ void dev_post(GraphView g, BfsBufs b, int lvl, BfsTun
 // within `radius` hops: radius h-1 adds min(row length, wdeg) per source bit,
 // radius h-2 adds the rest, wdeg - min(row length, wdeg), for the sources
 // already that close. One thread per vertex of T; plain adds (each vertex is
-// once in T), saturating at INT_MAX.
+// once in T), saturating at INT_MAX. Threads are taken from the last one
+// down, away from the warps that take a level's first work items when the
+// pass shares a phase with the level.
 template <int W>
 __device__ __forceinline__ void dev_weight_pass(const BfsBufs &b, const int32_t *src, const int32_t *rp,
                                                 const uint32_t *alive, bool last_radius)
 {
     const int32_t nt = b.ctl->t;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nt; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = nthr - 1 - ((int64_t)blockIdx.x * blockDim.x + threadIdx.x); i < nt; i += nthr) {
         const int32_t u = b.T[i];
         if (!is_alive(alive, u)) continue;
         long long sum = 0;
@@ -828,6 +923,7 @@ __device__ __forceinline__ void dev_end_fused(const BfsBufs &b, const int32_t *s
     const int64_t warp = tid >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int32_t nt = b.ctl->t;
+    const int32_t nq1 = b.ctl->q[(h - 1) % 3], nq2 = b.ctl->q[h % 3];
     for (int64_t base = warp * VPW; base < nt; base += nwarps * VPW) {
         const int64_t idx = base + grp;
         if (idx < nt) {
@@ -845,13 +941,17 @@ __device__ __forceinline__ void dev_end_fused(const BfsBufs &b, const int32_t *s
             }
         }
     }
-    clear_slot<W>(b, (h - 1) % 3);
-    clear_slot<W>(b, h % 3);
-    if (tid < ns) {
-        const int32_t c = b.cnt[tid];
-        b.cnt[tid] = 0;
-        if (deg && !slack) deg[src[tid]] = c;
-        if (pmin) atomicMin(&pmin->ming[pmin->gid ? __ldg(&pmin->gid[src[tid]]) : 0], c);
+    // the other pieces start at other warps (their load chains run side by
+    // side): the two slots at a third and two thirds of the grid, the
+    // sources from the last thread down
+    clear_slot<W>(b, (h - 1) % 3, nq1, nwarps / 3);
+    clear_slot<W>(b, h % 3, nq2, 2 * nwarps / 3);
+    const int64_t si = (int64_t)gridDim.x * blockDim.x - 1 - tid;
+    if (si < ns) {
+        const int32_t c = b.cnt[si];
+        b.cnt[si] = 0;
+        if (deg && !slack) deg[src[si]] = c;
+        if (pmin) atomicMin(&pmin->ming[pmin->gid ? __ldg(&pmin->gid[src[si]]) : 0], c);
     }
 }
 

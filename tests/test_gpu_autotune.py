@@ -42,14 +42,15 @@ def test_round_kernel_residency_does_not_change_results(kh):
     for h in (2, 3):
         want = oracle.peel(g, h)
         rounds = None
-        for blocks in (1, 2):
+        for blocks, sms in ((1, 0), (2, 0), (1, 7), (2, 1), (1, 76)):
             with kh.KHCore.from_graph(g) as ctx:
                 kh.khcore_set_round_blocks(ctx.ctx, blocks)
+                kh.khcore_set_round_sms(ctx.ctx, sms)
                 c, r, _ = ctx.decompose_ex(h)
-            assert np.array_equal(c, want), (h, blocks)
+            assert np.array_equal(c, want), (h, blocks, sms)
             if rounds is None:
                 rounds = r
-            assert np.array_equal(r, rounds), (h, blocks)
+            assert np.array_equal(r, rounds), (h, blocks, sms)
 
 
 def test_knob_arguments_are_checked(kh):
@@ -59,7 +60,9 @@ def test_knob_arguments_are_checked(kh):
                     lambda: kh.khcore_set_degree_classes(ctx.ctx, -1, 5),
                     lambda: kh.khcore_set_block_size(ctx.ctx, 300),
                     lambda: kh.khcore_set_block_graph_max(ctx.ctx, -2),
-                    lambda: kh.khcore_set_round_blocks(ctx.ctx, 3)]:
+                    lambda: kh.khcore_set_round_blocks(ctx.ctx, 3),
+                    lambda: kh.khcore_set_round_sms(ctx.ctx, -1),
+                    lambda: kh.khcore_set_round_sms(ctx.ctx, 100000)]:
             with pytest.raises(kh.KHCoreError):
                 bad()
 
