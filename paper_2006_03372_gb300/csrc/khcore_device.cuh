@@ -665,6 +665,34 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
             const int32_t dyg = __shfl_sync(kFull, dy, lane & ~(W - 1));
             if (fresh) acc.scanned += (unsigned long long)__popcll(fresh) * (unsigned long long)dyg;
         };
+        // The last fused level with one-word rows (a small frontier): the
+        // next-frontier row takes the atomicOr beside the load of V (the last
+        // level writes no V), a bit is new when neither had it, and the one
+        // writer that finds the row empty lists y for the clearing at the
+        // batch's end; no frontier flag is claimed.
+        auto edge_last1 = [&](int32_t e, int32_t e1, uint64_t fx) {
+            int32_t y = -1;
+            uint64_t fresh = 0;
+            bool listed = false, seen = false;
+            if (e < e1) {
+                y = __ldg(&col[e]);
+                if (fx && is_alive(alive, y)) {
+                    const uint64_t v = V[y];
+                    const unsigned long long old =
+                        atomicOr(reinterpret_cast<unsigned long long *>(&Fn[y]), (unsigned long long)fx);
+                    fresh = fx & ~(uint64_t)old & ~v;
+                    listed = old == 0;
+                    seen = v != 0;
+                    if (b.rowcnt) {
+                        const uint64_t rf = fresh & row_mask(0, b.row_first);
+                        if (rf) atomicAdd(&b.rowcnt[y], b.row_sign * __popcll(rf));
+                    }
+                }
+            }
+            swar_step<W>(sw, fresh & elig_mask(b, 0, y), cnt_s);
+            warp_append(listed, y, pick3(b.Q, nslot), &b.ctl->q[nslot]);
+            if (b.newcnt && listed && !seen) acc.newv++;
+        };
         // work items: up to C entries of one frontier row each, one warp per item
         for (int64_t it = warp; it < ni; it += nwarps) {  // warp-uniform
             const int2 item = Ic[it];
@@ -673,10 +701,16 @@ __device__ __forceinline__ void dev_level(GraphView g, const uint32_t *alive, Bf
             const int32_t e1 = item.y + C < rend ? item.y + C : rend;
             const uint64_t fx = Fc[(size_t)x * W + j];
             for (int32_t eb = item.y; eb < e1; eb += SLOTS) {
-                if constexpr (FUSED && !LAST)
+                if constexpr (FUSED && !LAST) {
                     edge_fused(eb + slot, e1, fx);
-                else
+                } else if constexpr (FUSED && LAST && W == 1) {
+                    if (probe)
+                        edge(eb + slot, e1, fx);
+                    else
+                        edge_last1(eb + slot, e1, fx);
+                } else {
                     edge(eb + slot, e1, fx);
+                }
             }
         }
     } else {
@@ -931,11 +965,15 @@ __device__ __forceinline__ void dev_end_fused(const BfsBufs &b, const int32_t *s
             b.V[(size_t)u * W + j] = 0;
             if (j == 0) {
                 flag_clear(b.tflag, u);
-                if (slack && is_alive(alive, u)) {
-                    const int32_t d = deg[u];
-                    const int32_t ex = min(nt, b.wsum ? b.wsum[u] : nt);
-                    const long long sl = (long long)slack[u] + ex;
-                    slack[u] = (int32_t)(sl < d ? sl : d);
+                if (slack) {
+                    // loaded together with the alive bit (one round trip)
+                    const bool al = is_alive(alive, u);
+                    const int32_t d = deg[u], s0 = slack[u];
+                    const int32_t ws = b.wsum ? b.wsum[u] : nt;
+                    if (al) {
+                        const long long sl = (long long)s0 + min(nt, ws);
+                        slack[u] = (int32_t)(sl < d ? sl : d);
+                    }
                 }
                 if (b.wsum) b.wsum[u] = 0;
             }
@@ -1011,21 +1049,24 @@ __device__ __forceinline__ void dev_min_alive_deg(int32_t n, const uint32_t *ali
     if (p.G == 1) {
         __shared__ int32_t red[3][32];
         int32_t me = INT_MAX, ml = INT_MAX, mu = INT_MAX;
-        // U words per warp step, their loads issued together (the scan is
-        // latency-bound: a handful of words per warp)
-        constexpr int U = 4;
+        // U words per warp step, the alive words and the degrees and slacks
+        // loaded together whatever the alive bits (one round trip per step;
+        // the scan is latency-bound: a handful of words per warp)
+        constexpr int U = 8;
         for (int64_t w0 = warp * U; w0 < nw; w0 += nwarps * U) {
             uint32_t aw[U];
-#pragma unroll
-            for (int u = 0; u < U; u++) aw[u] = (w0 + u < nw) ? alive[w0 + u] : 0u;
             int32_t d[U], sl[U];
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 const int32_t v = (int32_t)(w0 + u) * 32 + lane;
-                const bool a = ((aw[u] >> lane) & 1u) && v < n;
-                d[u] = a ? deg[v] : INT_MAX;
-                sl[u] = (a && p.slack) ? p.slack[v] : 0;
+                const bool in = w0 + u < nw && v < n;
+                aw[u] = (w0 + u < nw) ? alive[w0 + u] : 0u;
+                d[u] = in ? deg[v] : INT_MAX;
+                sl[u] = (in && p.slack) ? p.slack[v] : 0;
             }
+#pragma unroll
+            for (int u = 0; u < U; u++)
+                if (!((aw[u] >> lane) & 1u)) d[u] = INT_MAX;
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 if (d[u] == INT_MAX) continue;
@@ -1105,25 +1146,41 @@ __device__ __forceinline__ void dev_refine_select(int32_t n, const uint32_t *ali
         const int32_t T = max(p.kg[0], min(p.ming[0], p.minub[0]));
         if (p.mind[0] > T) return;
         int32_t *cand0 = cand + __ldg(&p.cls_off[0]);
-        constexpr int U = 4;
+        // U words per warp step: alive words, slacks and degrees loaded
+        // together, one list atomic per step
+        constexpr int U = 8;
+        const unsigned lt = lanemask_lt();
         for (int64_t w0 = warp * U; w0 < nw; w0 += nwarps * U) {
             uint32_t aw[U];
-#pragma unroll
-            for (int u = 0; u < U; u++) aw[u] = (w0 + u < nw) ? alive[w0 + u] : 0u;
             int32_t d[U], sl[U];
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 const int32_t v = (int32_t)(w0 + u) * 32 + lane;
-                const bool a = ((aw[u] >> lane) & 1u) && v < n;
-                sl[u] = a ? p.slack[v] : 0;
-                d[u] = a ? deg[v] : 0;
+                const bool in = w0 + u < nw && v < n;
+                aw[u] = (w0 + u < nw) ? alive[w0 + u] : 0u;
+                sl[u] = in ? p.slack[v] : 0;
+                d[u] = in ? deg[v] : 0;
             }
+            unsigned m[U];
+            int32_t tot = 0;
 #pragma unroll
             for (int u = 0; u < U; u++) {
-                const int32_t v = (int32_t)(w0 + u) * 32 + lane;
-                const bool pick = sl[u] > 0 && d[u] - sl[u] <= T;
-                if (pick) p.slack[v] = 0;
-                warp_append(pick, v, cand0, &p.ncand[0]);
+                const bool pick = ((aw[u] >> lane) & 1u) && sl[u] > 0 && d[u] - sl[u] <= T;
+                m[u] = __ballot_sync(kFull, pick);
+                tot += __popc(m[u]);
+            }
+            if (tot == 0) continue;  // warp-uniform
+            int32_t base = 0;
+            if (lane == 0) base = atomicAdd(&p.ncand[0], tot);
+            base = __shfl_sync(kFull, base, 0);
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                if ((m[u] >> lane) & 1u) {
+                    const int32_t v = (int32_t)(w0 + u) * 32 + lane;
+                    p.slack[v] = 0;
+                    cand0[base + __popc(m[u] & lt)] = v;
+                }
+                base += __popc(m[u]);
             }
         }
         return;
@@ -1208,7 +1265,8 @@ __device__ __forceinline__ void dev_set_level(PeelView p, PeelState *st)
 __device__ __forceinline__ void dev_set_level_serial(PeelView p, PeelState *st) { set_level_part(p, st, 0, 1, true); }
 
 // D = {alive v : deg[v] <= k_g(v)}: core[v] = k, rnd[v] = round, clear the
-// alive bit, append v to dlist (st->aq[0]) and to its class region of dcls.
+// alive bit, append v to dlist (st->aq[0]; skipped when dlist is null) and to
+// its class region of dcls.
 // vis is rewritten whole: exactly the bits of D. A warp owns one 32-vertex
 // word of each bitset.
 __device__ __forceinline__ void dev_peel_compact(int32_t n, const int32_t *rp,
@@ -1236,13 +1294,15 @@ __device__ __forceinline__ void dev_peel_compact(int32_t n, const int32_t *rp,
         if (lane == 0) {
             alive[w] = aw & ~mask;
             if (vis) vis[w] = mask;  // every word of vis is written: it starts the round's affected BFS
-            base = atomicAdd(&st->aq[0], __popc(mask));
+            if (dlist) base = atomicAdd(&st->aq[0], __popc(mask));
             atomicAdd(&st->nD, __popc(mask));
             atomicSub(&st->alive, __popc(mask));
             atomicAdd(&st->m_alive, 0ull - dsum);
         }
-        base = __shfl_sync(kFull, base, 0);
-        if (del) dlist[base + __popc(mask & lanemask_lt())] = y;
+        if (dlist) {  // uniform
+            base = __shfl_sync(kFull, base, 0);
+            if (del) dlist[base + __popc(mask & lanemask_lt())] = y;
+        }
         // class regions of the deleted-source lists
         const int32_t cy = del ? __ldg(&p.cls[gy]) : -1;
         const int32_t c0 = __shfl_sync(kFull, cy, __ffs(mask) - 1);
@@ -1252,25 +1312,59 @@ __device__ __forceinline__ void dev_peel_compact(int32_t n, const int32_t *rp,
             dcls[__ldg(&p.cls_off[cy]) + atomicAdd(&p.nDc[cy], 1)] = y;
         }
     };
-    if (p.G == 1 && !vis) {
-        // one graph, no affected-set bits to write: U words per warp step,
-        // their loads issued together; only words that lose a vertex go on
+    if (p.G == 1 && !vis && !dlist) {
+        // one graph, neither affected-set bits nor list to write (lazy mode):
+        // U words per warp step, alive words and degrees loaded together,
+        // one set of counter atomics and one class-list atomic per step
         const int32_t k = p.kg[0];
-        constexpr int U = 4;
+        const int32_t c0 = __ldg(&p.cls[0]);
+        int32_t *dc = dcls + __ldg(&p.cls_off[c0]);
+        const unsigned lt = lanemask_lt();
+        constexpr int U = 8;
         for (int64_t w0 = warp * U; w0 < nw; w0 += nwarps * U) {
             uint32_t aw[U];
-#pragma unroll
-            for (int u = 0; u < U; u++) aw[u] = (w0 + u < nw) ? alive[w0 + u] : 0u;
-            bool del[U];
+            int32_t d[U];
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 const int32_t y = (int32_t)(w0 + u) * 32 + lane;
-                del[u] = ((aw[u] >> lane) & 1u) && y < n && deg[y] <= k;
+                aw[u] = (w0 + u < nw) ? alive[w0 + u] : 0u;
+                d[u] = (w0 + u < nw && y < n) ? deg[y] : INT_MAX;
             }
+            unsigned m[U];
+            int32_t tot = 0;
 #pragma unroll
             for (int u = 0; u < U; u++) {
-                const unsigned mask = __ballot_sync(kFull, del[u]);
-                if (mask) peel_word(w0 + u, aw[u], mask, del[u], (int32_t)(w0 + u) * 32 + lane, k, 0);
+                m[u] = __ballot_sync(kFull, ((aw[u] >> lane) & 1u) && d[u] <= k);
+                tot += __popc(m[u]);
+            }
+            if (tot == 0) continue;  // warp-uniform
+            int32_t base = 0;
+            if (lane == 0) base = atomicAdd(&p.nDc[c0], tot);
+            unsigned long long dsum = 0;
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                if ((m[u] >> lane) & 1u) {
+                    const int32_t y = (int32_t)(w0 + u) * 32 + lane;
+                    core[y] = k;
+                    if (rnd) rnd[y] = r;
+                    dsum += (unsigned long long)(rp[y + 1] - rp[y]);
+                }
+            }
+#pragma unroll
+            for (int off = 16; off; off >>= 1) dsum += __shfl_xor_sync(kFull, dsum, off);
+            if (lane == 0) {
+#pragma unroll
+                for (int u = 0; u < U; u++)
+                    if (m[u]) alive[w0 + u] = aw[u] & ~m[u];
+                atomicAdd(&st->nD, tot);
+                atomicSub(&st->alive, tot);
+                atomicAdd(&st->m_alive, 0ull - dsum);
+            }
+            base = __shfl_sync(kFull, base, 0);
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                if ((m[u] >> lane) & 1u) dc[base + __popc(m[u] & lt)] = (int32_t)(w0 + u) * 32 + lane;
+                base += __popc(m[u]);
             }
         }
         return;

@@ -328,8 +328,9 @@ __global__ void __launch_bounds__(kBlock, MINB) k_decompose(PersistArgs a)
             if (!grid_sync(a.gs, a.timeout_ns, Nop{})) return;
         }
         // peel set D
+        // (lazy mode: no affected-set BFS, so neither its bits nor its list)
         dev_peel_compact(a.g.n, a.g.row_ptr, a.alive, a.deg, a.p, a.st, a.core, a.rnd, lazy ? nullptr : a.vis,
-                         a.aq[0], a.dcls);
+                         lazy ? nullptr : a.aq[0], a.dcls);
         if (lazy) {
             // One BFS seeded at the deleted set of each class does what the
             // affected-set BFS and the update did: every alive vertex it
