@@ -874,14 +874,25 @@ __device__ __forceinline__ void dev_post(GraphView g, BfsBufs b, int lvl, BfsTun
 // down, away from the warps that take a level's first work items when the
 // pass shares a phase with the level.
 template <int W>
+//
+// slack (lazy mode's batch seeded at the deleted set, last radius; else
+// nullptr): wsum[u] is then final, and u widens its slack by
+// min(|T|, wsum[u]) (Observation 2: what it loses besides the sources it still
+// reaches lies within h-1 of them), capped at deg[u] read during the level
+// (any value at least the final one keeps deg - slack a lower bound). The
+// last level writes no T, so |T| is final too.
 __device__ __forceinline__ void dev_weight_pass(const BfsBufs &b, const int32_t *src, const int32_t *rp,
-                                                const uint32_t *alive, bool last_radius)
+                                                const uint32_t *alive, bool last_radius, int32_t *slack = nullptr,
+                                                const int32_t *deg = nullptr)
 {
     const int32_t nt = b.ctl->t;
     const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = nthr - 1 - ((int64_t)blockIdx.x * blockDim.x + threadIdx.x); i < nt; i += nthr) {
         const int32_t u = b.T[i];
         if (!is_alive(alive, u)) continue;
+        const int32_t w0 = b.wsum[u];
+        const int32_t s0 = slack ? slack[u] : 0;
+        const int32_t du = slack ? deg[u] : 0;
         long long sum = 0;
 #pragma unroll 1
         for (int j = 0; j < W; j++) {
@@ -895,7 +906,12 @@ __device__ __forceinline__ void dev_weight_pass(const BfsBufs &b, const int32_t 
                 sum += last_radius ? r1 : wd - r1;
             }
         }
-        if (sum) b.wsum[u] = (int32_t)min((long long)b.wsum[u] + sum, (long long)INT_MAX);
+        const int32_t ws = (int32_t)min((long long)w0 + sum, (long long)INT_MAX);
+        if (sum) b.wsum[u] = ws;
+        if (slack) {
+            const long long sl = (long long)s0 + min(nt, ws);
+            slack[u] = (int32_t)(sl < du ? sl : du);
+        }
     }
 }
 
@@ -933,21 +949,18 @@ __device__ __forceinline__ void dev_end(BfsBufs b, const int32_t *src, int32_t n
 }
 
 
-// End of a batch run with fused levels: zero the V rows and tflag of T, the
-// frontier rows and flags of the last level's slot and of the slot its push
-// direction wrote, and the per-source counts. Per source position i < ns:
-// when deg is set, deg[src[i]] = its count; when p.ming is set too, the count
-// also goes into its graph's exact minimum (the refine step of the lazy
-// mode). When slack is set (the lazy mode's batch seeded at the deleted set,
-// whose row counts were already taken off deg), every alive vertex of T (the
-// vertices within h-1 of the sources) widens its slack by
-// min(extra, wsum[u]) (Observation 2: what it loses beyond the sources it
-// still reaches lies within h-1 of them), extra = |T| (those vertices plus
-// the sources), capped so that deg - slack stays >= 0; wsum is reset.
+// End of a batch run with fused levels: zero the V rows and tflag of T (and
+// wsum, when set), the frontier rows and flags of the last level's slot and
+// of the slot its push direction wrote, and the per-source counts. Per source
+// position i < ns: when deg is set, deg[src[i]] = its count; when p.ming is
+// set too, the count also goes into its graph's exact minimum (the refine
+// step of the lazy mode). Nothing here reads what a phase running beside it
+// writes, other than these rows (the lazy mode's batch seeded at the deleted
+// set ends inside the next round's minimum scan; its slack update ran in the
+// weight pass of its last level).
 template <int W>
 __device__ __forceinline__ void dev_end_fused(const BfsBufs &b, const int32_t *src, int32_t ns, int32_t h,
-                                              int32_t *deg, const PeelView *pmin, int32_t *slack,
-                                              const uint32_t *alive)
+                                              int32_t *deg, const PeelView *pmin)
 {
     const int lane = threadIdx.x & 31;
     const int j = lane % W;
@@ -965,16 +978,6 @@ __device__ __forceinline__ void dev_end_fused(const BfsBufs &b, const int32_t *s
             b.V[(size_t)u * W + j] = 0;
             if (j == 0) {
                 flag_clear(b.tflag, u);
-                if (slack) {
-                    // loaded together with the alive bit (one round trip)
-                    const bool al = is_alive(alive, u);
-                    const int32_t d = deg[u], s0 = slack[u];
-                    const int32_t ws = b.wsum ? b.wsum[u] : nt;
-                    if (al) {
-                        const long long sl = (long long)s0 + min(nt, ws);
-                        slack[u] = (int32_t)(sl < d ? sl : d);
-                    }
-                }
                 if (b.wsum) b.wsum[u] = 0;
             }
         }
@@ -988,7 +991,7 @@ __device__ __forceinline__ void dev_end_fused(const BfsBufs &b, const int32_t *s
     if (si < ns) {
         const int32_t c = b.cnt[si];
         b.cnt[si] = 0;
-        if (deg && !slack) deg[src[si]] = c;
+        if (deg) deg[src[si]] = c;
         if (pmin) atomicMin(&pmin->ming[pmin->gid ? __ldg(&pmin->gid[src[si]]) : 0], c);
     }
 }

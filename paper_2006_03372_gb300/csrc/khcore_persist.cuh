@@ -127,6 +127,16 @@ struct BatchOpt {
     bool lazy_end = false;      // lazy mode, seeded at the deleted set: slack update of T at the end
     bool min_fold = false;      // fold the sources' h-degrees into their graph's exact minimum
     bool pre_reset = false;     // the caller's last barrier already reset the ring for the first batch
+    bool defer_end = false;     // return after the last level; the caller runs the end (DeferredEnd)
+};
+
+// The end of a batch that the caller runs later, beside other work (the
+// deleted set's last batch: in the next round's minimum scan).
+struct DeferredEnd {
+    bool pending = false;
+    bool one_word = false;  // the batch's row layout: 1 word, else W
+    const int32_t *src = nullptr;
+    int32_t ns = 0, h = 0;
 };
 
 // The level ring's reset for a batch of ns sources, in a barrier's serial step.
@@ -207,23 +217,29 @@ __device__ bool bfs_batch(const PersistArgs &a, const int32_t *src, int32_t ns, 
         if (lvl == h - 1) {
             // the last level writes neither V nor T, so the weights of the
             // sources within h-1 are taken in the same phase
-            if (b.wsum && h >= 2) dev_weight_pass<W>(b, src, a.g.row_ptr, a.alive, true);
+            if (b.wsum && h >= 2)
+                dev_weight_pass<W>(b, src, a.g.row_ptr, a.alive, true, o.lazy_end ? a.p.slack : nullptr, a.deg);
             dev_level<W, true, true>(a.g, a.alive, b, lvl, tune);
         } else {
             dev_level<W, false, true>(a.g, a.alive, b, lvl, tune);
         }
     }
+    if (o.defer_end) return true;
     if (!grid_sync(a.gs, a.timeout_ns, [&] {
             if (o.lazy_end) a.ps->affected_total += ctl->t - ns;  // the vertices within h-1
         }))
         return false;
-    dev_end_fused<W>(b, src, ns, h, a.deg, o.min_fold ? &a.p : nullptr, o.lazy_end ? a.p.slack : nullptr, a.alive);
+    // the lazy mode's deleted-set batch writes no degrees (its row counts
+    // came off them during the levels)
+    dev_end_fused<W>(b, src, ns, h, o.lazy_end ? nullptr : a.deg, o.min_fold ? &a.p : nullptr);
     return true;
 }
 
 // h-degrees (or row counts) of src[0..ns) in batches of 64*W sources.
+// defer: the last batch's end is left to the caller, described in *def.
 template <int W>
-__device__ bool bfs_sources(const PersistArgs &a, const int32_t *src, int32_t ns, int32_t h, BatchOpt o)
+__device__ __forceinline__ bool bfs_sources(const PersistArgs &a, const int32_t *src, int32_t ns, int32_t h,
+                                            BatchOpt o, DeferredEnd *def = nullptr, bool defer = false)
 {
     constexpr int32_t S = 64 * W;
     const int32_t row_first = o.row_first;
@@ -231,13 +247,21 @@ __device__ bool bfs_sources(const PersistArgs &a, const int32_t *src, int32_t ns
         const int32_t cur = ns - off < S ? ns - off : S;
         o.row_first = row_first > off ? row_first - off : 0;
         if (off > 0) o.pre_reset = false;  // only the first batch can be pre-reset
+        o.defer_end = def && defer && off + cur == ns;
         // a batch of at most 64 sources runs on one-word rows: a quarter of
         // the row traffic of W = 4 for the same result (the row arrays are
         // all zero between batches in either layout)
-        const bool ok = (W > 1 && cur <= 64) ? bfs_batch<1>(a, src + off, cur, h, o)
-                                             : bfs_batch<W>(a, src + off, cur, h, o);
+        const bool one = W > 1 && cur <= 64;
+        const bool ok = one ? bfs_batch<1>(a, src + off, cur, h, o) : bfs_batch<W>(a, src + off, cur, h, o);
         if (!ok) return false;
         if (blockIdx.x == 0 && threadIdx.x == 0) a.ps->source_batches++;
+        if (o.defer_end) {
+            def->pending = true;
+            def->one_word = one || W == 1;
+            def->src = src + off;
+            def->ns = cur;
+            def->h = h;
+        }
     }
     return true;
 }
@@ -268,15 +292,28 @@ __global__ void __launch_bounds__(kBlock, MINB) k_decompose(PersistArgs a)
     // kernels at the widest W); the rounds follow
     const bool serial_level = a.p.G <= kSerialLevelMaxGraphs;
     const bool lazy = a.p.slack != nullptr;
+    DeferredEnd def;  // the deleted set's last batch (lazy mode, one class)
     for (bool first = true;; first = false) {
         // level of every graph: k_g <- max(k_g, min alive h-degree); the
         // barrier closing the previous round advances the round counter
         if (!grid_sync(a.gs, a.timeout_ns, [&] {
                 if (!first) a.st->round++;
                 a.st->lvl_set = 0;
+                if (def.pending) a.ps->affected_total += a.b.ctl->t - def.ns;  // the vertices within h-1
             }))
             return;
         mark(4);
+        if (def.pending) {
+            // the end of the previous round's last batch, beside the scan:
+            // it clears BFS rows, the scan reads alive, deg and slack
+            BfsBufs bd = a.b;
+            bd.wsum = a.wsum;
+            if (def.one_word)
+                dev_end_fused<1>(bd, def.src, def.ns, def.h, nullptr, nullptr);
+            else
+                dev_end_fused<W>(bd, def.src, def.ns, def.h, nullptr, nullptr);
+            def.pending = false;
+        }
         dev_min_alive_deg(a.g.n, a.alive, a.deg, a.p);
         if (lazy) {
             // lazy mode: exact recompute of the vertices whose bounds leave
@@ -358,7 +395,8 @@ __global__ void __launch_bounds__(kBlock, MINB) k_decompose(PersistArgs a)
                 o.row_sign = -1;
                 o.weights = true;
                 o.lazy_end = true;
-                if (!bfs_sources<W>(a, a.dcls + a.cls_off[c], nd, a.cls_h[c], o)) return;
+                if (!bfs_sources<W>(a, a.dcls + a.cls_off[c], nd, a.cls_h[c], o, &def, a.ncls == 1))
+                    return;
             }
             continue;
         }
