@@ -194,7 +194,11 @@ khcore_status khcore_hdegrees_of(khcore_ctx *ctx, int32_t h, int32_t count, cons
  * KHCORE_EINVAL. Messages: khcore_last_error(NULL), per host thread.
  * Set-up: the first call on a device, with that device current, looks up
  * the array's device address (cudaGetSymbolAddress) and caches it for that
- * device ordinal; make that first call before any stream capture begins.
+ * device ordinal. Under lazy module loading (the CUDA default) that first
+ * lookup is also when the device reserves the array, so make the first call
+ * during set-up, where allocation is allowed. Every call reads status words
+ * back and synchronises its stream, so no call can be captured into a CUDA
+ * graph.
  * cudaDeviceReset between calls is not supported: it discards the device's
  * copy of the array, and the cached address would then be stale.
  * Sharing: every call on a device uses the same array, and each call clears
