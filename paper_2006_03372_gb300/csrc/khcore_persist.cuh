@@ -4,10 +4,13 @@
 // round's counts before planning the recompute; on graphs that need tens of
 // thousands of rounds that launch-and-wait cost dominates. Here one persistent
 // kernel (grid = every block that can be resident, launched cooperatively so
-// that all blocks run at once) steps through the same phases:
-//   [level min -> set level -> peel set -> affected BFS
-//   -> recompute / outer-shell update] per round, after the initial h-degrees
-// separated by grid barriers. The decisions between phases (batch plans,
+// that all blocks run at once) steps through the same phases, separated by
+// grid barriers, after the initial h-degrees. Per round, in the default lazy
+// mode: level minimum -> bound check -> exact recompute of the candidates ->
+// set level -> peel set -> one BFS from the deleted set that updates the
+// bounds (its last batch's end runs beside the next round's minimum). In the
+// eager mode: level minimum -> set level -> peel set -> affected BFS ->
+// recompute / outer-shell update. The decisions between phases (batch plans,
 // push or pull, the end of the loop) read device counters after a barrier,
 // so every block takes the same path. Small serial steps (resetting counters,
 // snapshots, statistics) run in the barrier itself, on the block that arrives
@@ -154,7 +157,8 @@ __device__ __forceinline__ void reset_ring(LevelCtl *ctl, int32_t ns)
 // block taking part, with fused levels (dev_level<W, LAST, true>): a barrier
 // to reset the level ring, one phase per level, one to finish (h + 2
 // barriers; one more before level h-2 for the h-2 ball weights when h >= 3).
-// Returns false on timeout.
+// With o.defer_end it returns after the last level and the caller runs the
+// end later (h + 1). Returns false on timeout.
 template <int W>
 __device__ bool bfs_batch(const PersistArgs &a, const int32_t *src, int32_t ns, int32_t h, const BatchOpt &o)
 {
