@@ -127,7 +127,8 @@ struct BatchOpt {
     int32_t row_first = 0;
     int32_t row_sign = 1;       // -1: the row counts are taken off rowcnt
     bool weights = false;       // lazy mode, seeded at the deleted set: ball bounds into wsum
-    bool lazy_end = false;      // lazy mode, seeded at the deleted set: slack update of T at the end
+    bool lazy_end = false;      // lazy mode, seeded at the deleted set: slack update of T (in the
+                                // last level's weight pass), no degree writes at the end
     bool min_fold = false;      // fold the sources' h-degrees into their graph's exact minimum
     bool pre_reset = false;     // the caller's last barrier already reset the ring for the first batch
     bool defer_end = false;     // return after the last level; the caller runs the end (DeferredEnd)
